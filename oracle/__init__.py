@@ -25,11 +25,12 @@ Every reading of a garbled, ambiguous or silent passage is listed in the module 
 takes it and gathered in the design notes of the repository.
 """
 from .model import (Params, phi, dphi, window_offsets, norm_constant, velocity, forward,
-                    forward_final, jacobian_transpose_apply, control_derivative,
+                    forward_final, jacobian_transpose_apply, control_derivative, velocity_at,
+                    jacobian_transpose_apply_at,
                     adjoint_step, adjoint, project)
 from .tv import (grad, grad_T, grad_matrix, shrink, project_ball, cost_J, cost_K, cost_L,
                  cost_Ltilde, dLtilde_dc, dJ_dc, terminal_adjoint, dual_ascent, alm_stats)
-from .solve import SolveOpts, dal_iteration, admm_solve, dal_solve
+from .solve import SolveOpts, dal_iteration, admm_solve, dal_solve, free_components
 from .labels import cluster_labels, cluster_labels_bfs, label_agreement
 
 __all__ = [n for n in dir() if not n.startswith("_")]

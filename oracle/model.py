@@ -210,3 +210,52 @@ def project(eps: np.ndarray, p: Params) -> np.ndarray:
     lo = np.asarray(p.eps_lo, dtype=np.float64)
     hi = np.asarray(p.eps_hi, dtype=np.float64)
     return np.minimum(np.maximum(np.asarray(eps, dtype=np.float64), lo), hi)
+
+
+def velocity_at(c: np.ndarray, rows, cols, eps_x: float, eps_c: float, p: Params) -> np.ndarray:
+    """F_i (Eq. MAsystem) at the listed pixels only, one pixel at a time: for checking
+    samples of a full-size field.  Returns shape (len(rows), C)."""
+    H, W, C = c.shape
+    hx, hy = 1.0 / W, 1.0 / H
+    M = norm_constant(H, W, p)
+    out = np.zeros((len(rows), C))
+    for n, (r, q) in enumerate(zip(rows, cols)):
+        r0, r1 = max(0, r - p.radius), min(H, r + p.radius + 1)
+        q0, q1 = max(0, q - p.radius), min(W, q + p.radius + 1)
+        win = c[r0:r1, q0:q1]
+        dr = (np.arange(r0, r1) - r)[:, None]
+        dq = (np.arange(q0, q1) - q)[None, :]
+        delta = win - c[r, q]
+        d2 = (dq * hx) ** 2 + (dr * hy) ** 2
+        rr = 0.5 * eps_x * d2 + 0.5 * eps_c * np.sum(delta * delta, axis=-1)
+        w = phi(rr)
+        w[r - r0, q - q0] = 0.0          # j != i
+        out[n] = np.sum(w[..., None] * delta, axis=(0, 1)) / M
+    return out
+
+
+def jacobian_transpose_apply_at(c: np.ndarray, lam: np.ndarray, rows, cols, eps_x: float,
+                                eps_c: float, p: Params) -> np.ndarray:
+    """(dF/dc)^T lam at the listed pixels k, one pixel at a time: row k collects
+    dF_i/dc_k^T lam_i from every agent i with k in W(i), plus the diagonal block
+    dF_k/dc_k^T lam_k = -sum_{j in W(k)} dF_k/dc_j^T lam_k (Section 3.1)."""
+    H, W, C = c.shape
+    hx, hy = 1.0 / W, 1.0 / H
+    M = norm_constant(H, W, p)
+    out = np.zeros((len(rows), C))
+    for n, (r, q) in enumerate(zip(rows, cols)):
+        acc = np.zeros(C)
+        for oy in range(-p.radius, p.radius + 1):
+            for ox in range(-p.radius, p.radius + 1):
+                ri, qi = r + oy, q + ox          # the other agent of the pair
+                if (oy, ox) == (0, 0) or not (0 <= ri < H and 0 <= qi < W):
+                    continue
+                # k is in W(i) exactly when i is in W(k) (symmetric window)
+                delta = c[r, q] - c[ri, qi]      # c_k - c_i
+                rr = 0.5 * eps_x * ((ox * hx) ** 2 + (oy * hy) ** 2) + 0.5 * eps_c * np.dot(delta, delta)
+                # off-diagonal: block dF_i/dc_k applied to lam_i
+                acc += (dphi(rr) * eps_c * np.dot(delta, lam[ri, qi])) * delta + phi(rr) * lam[ri, qi]
+                # diagonal: minus block dF_k/dc_i (same r, delta -> -delta) applied to lam_k
+                acc -= (dphi(rr) * eps_c * np.dot(delta, lam[r, q])) * delta + phi(rr) * lam[r, q]
+        out[n] = acc / M
+    return out

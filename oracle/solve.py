@@ -7,15 +7,26 @@ Readings taken here (each also recorded in the design notes):
 * Search direction.  Algorithm 1 tests the trial control eps - tau D but then updates
   eps + sigma D.  With lambda(T) = -grad (Eq. opt_system-b), D^n is minus the gradient
   divided by dt, i.e. a descent direction, so the trial and the update both use
-  eps + tau D.  The Armijo test is L(Pi_E(eps + tau D)) <= L(eps) - c tau |D|^2 with
-  |D|^2 = dt sum_n |D^n|^2 (rectangular quadrature, Section 3.2), which is minus the
-  directional derivative along D.
+  eps + tau D.
+* Stationarity.  A component of D is active-blocked when the control sits on a bound of
+  E and D pushes it outward; the projection leaves it unchanged.  When every nonzero
+  component is blocked, the variational inequality of the Remark on convergence criteria
+  holds exactly (D . (e - eps) <= 0 for all e in E): the control is stationary and the
+  epsilon-step ends without trials.
+* Sufficient decrease.  The test is L(Pi_E(eps + tau D)) < L(eps) and
+  L(Pi_E(eps + tau D)) <= L(eps) - c tau |P D|^2, with |P D|^2 = dt sum_n |P D^n|^2
+  (rectangular quadrature, Section 3.2) and P D the direction with blocked components
+  zeroed.  Without active bounds P D = D, the printed test; with them, |P D|^2 is minus
+  the slope of L along the projected path, whereas the printed |D|^2 would demand a
+  decrease the projection cannot deliver and reject every step.  The strict inequality
+  is implied by the printed one in exact arithmetic; it stops the rounding of
+  L(eps) - c tau |P D|^2 from accepting a step that does not lower L.
 * Two-way loop.  Start at tau = sigma.  If the test fails, halve (tau <- b tau) until it
   passes; if it passes, double (tau <- tau / b) while it keeps passing and accept the
   last tau that passed (the printed loop would return the first failing tau).  At most
-  max_ls trials per iteration.  If no trial passes, or D = 0, the iteration is a stall:
-  eps and sigma are unchanged and the current epsilon-step ends (repeating it would
-  repeat the same trials).  sigma carries the accepted tau to the next iteration.
+  max_ls trials per iteration.  If no trial passes the iteration is a stall: eps and
+  sigma are unchanged and the current epsilon-step ends (repeating it would repeat the
+  same trials).  sigma carries the accepted tau to the next iteration.
 * Algorithm 2.  mu^(0) = 0 and eps^(0) = 57 (Section 3.2) unless given; the
   epsilon-argmin of line 5 is approximated by k_in DAL iterations at fixed
   (v^(j-1), mu^(j-1)); gamma = rho (Section 4.2).
@@ -79,7 +90,15 @@ class DalInfo:
     gnorm2: float
     tau: float
     trials: int
-    stalled: bool
+    stalled: bool            # the epsilon-step ends here (stationary or no admissible step)
+    stationary: bool = False
+
+
+def free_components(eps, D, p: Params) -> np.ndarray:
+    """Mask of the components of D that the projection onto E does not block."""
+    lo = np.asarray(p.eps_lo, dtype=np.float64)
+    hi = np.asarray(p.eps_hi, dtype=np.float64)
+    return (D != 0.0) & ((eps < hi) | (D < 0.0)) & ((eps > lo) | (D > 0.0))
 
 
 def dal_iteration(c0, eps, sigma, obj, p: Params, o: SolveOpts):
@@ -87,14 +106,15 @@ def dal_iteration(c0, eps, sigma, obj, p: Params, o: SolveOpts):
     traj = forward(c0, eps, p)
     L0 = obj.value(traj[-1])
     _, D = adjoint(traj, eps, -obj.gradient(traj[-1]), p)
-    gnorm2 = p.dt * float(np.sum(D * D))
-    if gnorm2 == 0.0:
-        return eps, sigma, DalInfo(L0, L0, 0.0, 0.0, 0, True)
+    free = free_components(eps, D, p)
+    gnorm2 = p.dt * float(np.sum(np.where(free, D, 0.0) ** 2))
+    if not np.any(free):
+        return eps, sigma, DalInfo(L0, L0, 0.0, 0.0, 0, True, True)
 
     def trial(tau):
         e = project(eps + tau * D, p)
         L = obj.value(forward_final(c0, e, p))
-        return L <= L0 - o.ls_c * tau * gnorm2, L, e
+        return (L < L0) and (L <= L0 - o.ls_c * tau * gnorm2), L, e
 
     tau = sigma
     ok, L, e = trial(tau)

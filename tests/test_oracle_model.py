@@ -7,7 +7,8 @@ all-pairs evaluation of Eq. MAsystem, and finite differences for every derivativ
 import numpy as np
 import pytest
 
-from oracle import (Params, phi, dphi, velocity, forward, forward_final,
+from oracle import (Params, phi, dphi, velocity, forward, forward_final, velocity_at,
+                    jacobian_transpose_apply_at,
                     jacobian_transpose_apply, control_derivative, adjoint, project,
                     window_offsets)
 from oracle.tv import cost_Ltilde, dLtilde_dc, cost_J, dJ_dc
@@ -238,3 +239,16 @@ def test_projection_is_box_clip():
     p = Params()
     e = np.array([[1.0, 5000.0], [57.0, -3.0], [2.0, 1100.0]])
     assert np.array_equal(project(e, p), np.array([[2.0, 1100.0], [57.0, 2.0], [2.0, 1100.0]]))
+
+
+def test_pointwise_evaluations_match_field_versions(rng):
+    c = rng.uniform(0.2, 0.7, size=(9, 13, 3))
+    lam = rng.normal(size=c.shape)
+    p = Params(radius=3)
+    rows = [0, 0, 4, 8, 8, 3]
+    cols = [0, 12, 6, 0, 12, 1]
+    F = velocity(c, 40.0, 12.0, p)
+    assert np.allclose(velocity_at(c, rows, cols, 40.0, 12.0, p), F[rows, cols], atol=1e-15)
+    JT = jacobian_transpose_apply(c, lam, 40.0, 12.0, p)
+    assert np.allclose(jacobian_transpose_apply_at(c, lam, rows, cols, 40.0, 12.0, p),
+                       JT[rows, cols], atol=1e-14)
