@@ -1,0 +1,464 @@
+"""Throughput benchmark: Mpixel-steps/s of the agent-based TV solve on GB300.
+
+Workload (one image per GPU): 1024 x 1024 RGB, 12 Voronoi regions, linear ramp 0.1,
+noise sigma 0.08; window radius 5, T = 50 Euler steps, 50 DAL iterations per multiplier
+step, the paper's constants otherwise (dt 0.25, E = [2, 1100]^2, eps0 = 57, rho = gamma
+= 1e-2, alpha = 3000, Armijo sigma0 = 1, b = 1/2, c = 1e-4).
+
+One step = one ADMM multiplier step (Algorithm 2): 50 iterations of Algorithm 1 (forward
+sweep with store, terminal adjoint, adjoint sweep, Armijo trial sweeps) then a forward
+sweep, pd_tv_step and alm_update, through solve(k_out = 1), continuing from the
+previous step's control, multiplier and Armijo step.  Pixel-steps counted = pixels x
+(Euler steps + adjoint steps + TV sweeps) the library reports it executed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank solves its own image (independent
+problems, weak scaling, no collective on the data path); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 1024
+C = 3
+R = 5
+T = 50
+K_IN = 50
+SEED = 0
+METRIC = "Mpixel-steps/s of forward+adjoint+PD sweep"
+UNIT = "Mpixel-steps/s"
+WORKLOAD = ("1024x1024x3 Voronoi(12 regions)+ramp 0.1+noise 0.08, window radius 5, T=50, "
+            "50 DAL iterations per ADMM multiplier step")
+
+
+def forward_flops_per_launch(h, w, c, r):
+    """Algorithmic FP32 flops of one Euler step: each unordered in-window pair once,
+    (7C + 9) flops per pair (FMA = 2): C differences, the squared colour distance, r_ij,
+    the Wendland polynomial, and the C updates of both agents."""
+    pairs2 = sum((h - abs(dy)) * (w - abs(dx)) for dy in range(-r, r + 1)
+                 for dx in range(-r, r + 1) if (dy, dx) != (0, 0))
+    return pairs2 / 2 * (7 * c + 9)
+
+
+# Algorithmic HBM bytes per pixel (float32 fields, C channels): each input field read
+# once, each output written once.
+BYTES_PER_PIXEL = {
+    "forward": lambda c: 8 * c,        # c^n -> c^{n+1}
+    "adjoint": lambda c: 12 * c,       # c^n, lambda^{n+1} -> lambda^n
+    "objective": lambda c: 24 * c,     # c, c0, v, mu -> L~ (Armijo trial)
+    "terminal": lambda c: 28 * c,      # c, c0, v, mu -> L~, lambda^T
+    "pd_tv_step": lambda c: 20 * c,    # c, mu -> v
+    "alm_update": lambda c: 44 * c,    # c, c_prev, c0, v, v_prev, mu -> mu
+}
+
+
+def adjoint_flops_per_launch(h, w, c, r):
+    """Algorithmic FP32 flops of one adjoint step, each unordered pair once: the kernel
+    and its derivative (phi, phi'), the colour distance, delta.dlam and both agents'
+    updates of J^T lam, and both agents' contributions to D: (11C + 18) per pair."""
+    pairs2 = sum((h - abs(dy)) * (w - abs(dx)) for dy in range(-r, r + 1)
+                 for dx in range(-r, r + 1) if (dy, dx) != (0, 0))
+    return pairs2 / 2 * (11 * c + 18)
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """152 SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) during the timed region."""
+
+    QUERY = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.split(", ") for l in self.file.read().strip().splitlines() if l.strip()]
+        os.unlink(self.file.name)
+        mine = [r for r in rows if len(r) >= 10 and
+                (self.bus_id is None or r[1].lower().endswith(self.bus_id.lower()[-12:]))]
+        if not mine:
+            mine = [r for r in rows if len(r) >= 10]
+        if not mine:
+            return None
+        sm = [float(r[2]) for r in mine if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in mine if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in mine for n, v in zip(names, r[6:10]) if v.strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(mine)}
+
+
+def measure_kernels(torch, lib, dev, stream, size: int, reps: int = 5, only: str | None = None):
+    """Average device time of each kernel on a size x size x 3 image, R = 5, with CUDA
+    events on the library's stream.  Fields of 4096^2 x 3 float32 (201 MB) exceed the
+    129 MB L2, so the HBM-bound kernels are measured against HBM, not L2."""
+    Hs = Ws = size
+    Cs = 3
+    rng = np.random.default_rng(7)
+    img = rng.uniform(0.3, 0.7, size=(Hs, Ws, Cs)).astype(np.float32)
+    p = lib.agents_default_params(Hs, Ws, Cs, R, reps)
+    out = {}
+    with lib.Context(p, torch.from_numpy(img).to(dev), stream) as ctx:
+        c = torch.from_numpy(img).to(dev)
+        c2 = c + 0.01
+        mu = torch.randn(Hs, Ws, 2, Cs, device=dev) * 0.5
+        v = torch.zeros_like(mu)
+        vp = torch.randn_like(mu)
+        lam = torch.empty_like(c)
+        st = torch.zeros(5, dtype=torch.float64, device=dev)
+        eps = np.full((reps, 2), 57.0)
+        D = torch.zeros(reps, 2, dtype=torch.float64, device=dev)
+        obj = torch.zeros(1, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()                    # inputs made on torch's stream
+
+        def timed(fn, n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fn()                                    # warm
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(n):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / 1e3 / n
+
+        runs = {
+            "forward": (lambda: lib.agents_forward(ctx.handle, eps, None, store=False), reps),
+            "objective": (lambda: lib.agents_objective(ctx.handle, c, v, mu, obj, None), 1),
+            "terminal": (lambda: lib.agents_objective(ctx.handle, c, v, mu, obj, lam), 1),
+            "pd_tv_step": (lambda: lib.pd_tv_step(ctx.handle, c, mu, v), 1),
+            "alm_update": (lambda: lib.alm_update(ctx.handle, c, c2, v, vp, mu, st), 1),
+        }
+        for name, (fn, launches) in runs.items():
+            if only and name != only:
+                continue
+            t = timed(fn, 5) / launches
+            out[name] = {"us": t * 1e6}
+        if only in (None, "adjoint"):
+            lib.agents_forward(ctx.handle, eps, None, store=True)
+            t_adj = timed(lambda: lib.agents_adjoint(ctx.handle, eps, v, mu, D, obj, None), 3)
+            t_term = out.get("terminal", {}).get("us", 0.0) / 1e6
+            out["adjoint"] = {"us": (t_adj - t_term) / reps * 1e6,
+                              "note": "per step; the terminal adjoint of the sweep subtracted"}
+    peaks = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    for name, rec in out.items():
+        t = rec["us"] / 1e6
+        if name in ("forward", "adjoint"):
+            fl = (forward_flops_per_launch if name == "forward" else adjoint_flops_per_launch)(
+                Hs, Ws, Cs, R)
+            rec.update({"bound": "alu", "achieved": fl / t / 1e12, "unit": "TFLOP/s",
+                        "peak": fp32_peak_tflops(sm_max)})
+        else:
+            by = BYTES_PER_PIXEL[name](Cs) * Hs * Ws
+            rec.update({"bound": "hbm", "achieved": by / t / 1e9, "unit": "GB/s", "peak": hbm,
+                        "bytes": by})
+        rec["frac"] = rec["achieved"] / rec["peak"]
+    return out
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+
+ORACLE_ROWS = 256
+ORACLE_SAMPLE = (f"top {ORACLE_ROWS} rows of the 1024x1024x3 image (R=5): one Euler step, one "
+                 "adjoint step, one v-step and one multiplier update, float64 NumPy, 1 thread")
+
+
+def oracle_sample():
+    """Time the FP64 oracle on one bounded sample of the workload: one Euler step, one
+    adjoint step, one v-step and one multiplier update on a 256 x 1024 band of the image
+    (the per-pixel work of the full image).  Returns (pixel-steps, seconds)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    import oracle
+    from oracle.tv import v_step, dual_ascent, alm_stats
+    from synth import make_image, THROUGHPUT_1024_RGB
+    c0 = make_image(THROUGHPUT_1024_RGB, SEED).astype(np.float32).astype(np.float64)
+    c0 = np.ascontiguousarray(c0[:ORACLE_ROWS])
+    p = oracle.Params(radius=R, nsteps=1)
+    mu = np.zeros((ORACLE_ROWS, W, 2, C))
+    eps = np.array([[57.0, 57.0]])
+    t0 = time.perf_counter()
+    traj = oracle.forward(c0, eps, p)
+    v = v_step(traj[-1], mu, p)
+    lamT = oracle.terminal_adjoint(traj[-1], v, mu, c0, p)
+    oracle.adjoint(traj, eps, lamT, p)
+    mu2 = dual_ascent(mu, v, traj[-1], p)
+    alm_stats(traj[-1], v, v, c0, c0, p)
+    dt = time.perf_counter() - t0
+    del mu2
+    return ORACLE_ROWS * W * 4, dt
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores: each step one bounded sample."""
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample()
+    total_px, total_s = 0, 0.0
+    for _ in range(args.steps):
+        px, s = oracle_sample()
+        total_px += px
+        total_s += s
+    value = total_px / total_s / 1e6
+    sample = ORACLE_SAMPLE
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample, "host_cores": cpu_cores()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--kernel-size", type=int, default=4096,
+                    help="image side for the per-kernel roofline table (0: skip)")
+    ap.add_argument("--kernel", default=None,
+                    help="only time this kernel at --kernel-size and exit (profiling driver)")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2510_16154_gb300 import lib
+    from paper_2510_16154_gb300.build import build
+    from synth import make_image, THROUGHPUT_1024_RGB
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    lib.load()
+    stream = torch.cuda.Stream(device=dev)
+    if args.kernel:
+        res = measure_kernels(torch, lib, dev, stream, args.kernel_size, only=args.kernel)
+        if rank == 0:
+            print(json.dumps({"kernel": args.kernel, "size": args.kernel_size, **res}), flush=True)
+        return 0
+
+    img = make_image(THROUGHPUT_1024_RGB, SEED + rank).astype(np.float32)
+    p = lib.agents_default_params(H, W, C, R, T)
+    ctx = lib.Context(p, torch.from_numpy(img).to(dev), stream)
+    eps = torch.full((T, 2), 57.0, dtype=torch.float64, device=dev)
+    mu = torch.zeros(H, W, 2, C, device=dev)
+    o = lib.agents_default_solve_opts()
+    o.k_out, o.k_in = 1, K_IN
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    torch.cuda.synchronize()                        # inputs made on torch's stream
+
+    def step():
+        info = lib.solve(ctx.handle, o, eps, mu)
+        o.sigma0 = info.final_sigma if info.final_sigma > 0 else o.sigma0
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id  # type: ignore[attr-defined]
+    except Exception:
+        pass
+    sampler = ClockSampler(bus)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    pixel_steps = 0
+    launches = 0
+    fwd = adj = tv = trials = 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                       # untimed: evict the previous step from L2
+            ev[k][0].record(stream)
+        info = step()
+        ev[k][1].record(stream)
+        pixel_steps += H * W * (info.forward_steps + info.adjoint_steps + info.tv_sweeps)
+        launches += info.kernel_launches
+        fwd += info.forward_steps
+        adj += info.adjoint_steps
+        tv += info.tv_sweeps
+        trials += info.trials
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    t_max = elapsed
+    total_ps = pixel_steps
+    if world > 1:
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        s = torch.tensor([float(pixel_steps)], dtype=torch.float64, device=dev)
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        total_ps = float(s.item())
+    value = total_ps / t_max / 1e6
+
+    # ---- roofline of the dominant kernel (the forward Euler step), timed live: one
+    # forward sweep of T launches on the library's stream, averaged per launch.
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eps_h = eps.cpu().numpy()
+    lib.agents_forward(ctx.handle, eps_h, None, store=False)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        flush.zero_()
+        e0.record(stream)
+    for _ in range(reps):
+        lib.agents_forward(ctx.handle, eps_h, None, store=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launch_s = e0.elapsed_time(e1) / 1e3 / (reps * T)
+    flops = forward_flops_per_launch(H, W, C, R)
+    achieved = flops / launch_s / 1e12
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(sm_max)
+    roofline = {"bound": "alu", "kernel": "forward_tile_kernel<5,3>", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_basis": f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (max SM clock)",
+                "launch_us": launch_s * 1e6,
+                "flops_per_launch": flops}
+
+    # ---- end to end through the public API with host buffers (pinned): the image,
+    # the control and the multiplier go in, the control, multiplier and colours come back.
+    e2e = None
+    if args.e2e_steps > 0:
+        img_h = torch.from_numpy(img).pin_memory()
+        eps_h2 = torch.from_numpy(eps.cpu().numpy()).pin_memory()
+        mu_h = mu.cpu().pin_memory()
+        c_h = torch.empty(H, W, C).pin_memory()
+        o2 = lib.agents_solve_opts.from_buffer_copy(o)
+        e2e_ps = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            lib.agents_set_image(ctx.handle, img_h)
+            info = lib.solve(ctx.handle, o2, eps_h2, mu_h, None, c_h)
+            o2.sigma0 = info.final_sigma if info.final_sigma > 0 else o2.sigma0
+            e2e_ps += H * W * (info.forward_steps + info.adjoint_steps + info.tv_sweeps)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        h2d = img_h.numel() * 4 + eps_h2.numel() * 8 + mu_h.numel() * 4
+        d2h = eps_h2.numel() * 8 + mu_h.numel() * 4 + c_h.numel() * 4
+        e2e = {"value": e2e_ps / t_e2e / 1e6 * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+               "timing": "host wall clock around solve() with pinned host buffers"}
+
+    kernels = None
+    if args.kernel_size > 0:
+        kernels = {"size": f"{args.kernel_size}x{args.kernel_size}x3, R={R}",
+                   **measure_kernels(torch, lib, dev, stream, args.kernel_size)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        px, s = oracle_sample()
+        cpu = {"value": px / s / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": ORACLE_SAMPLE,
+               "host_cores": cpu_cores(), "seconds": s}
+
+    ctx.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "H": H, "W": W, "C": C, "radius": R,
+                           "nsteps": T, "k_in": K_IN, "step": "one ADMM multiplier step",
+                           "l2": "flushed between steps (256 MB write, untimed)",
+                           "parallelism": f"replicas x{world} (one image per GPU)",
+                           "per_rank": {"forward_steps": fwd, "adjoint_steps": adj,
+                                        "tv_sweeps": tv, "armijo_trials": trials}},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches, "kernels": kernels}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

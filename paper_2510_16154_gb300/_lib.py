@@ -1,0 +1,252 @@
+"""ctypes binding of ``libagents.so`` (declared in ``include/agents.h``).
+
+Argument marshalling only: every function here forwards to the C entry point of the
+same name, converting arrays to raw pointers and raising :class:`AgentsError` on a
+non-zero status.  Arrays may be torch tensors (device or host) or numpy arrays (host);
+they must be C-contiguous with the dtype the header states.  No computation happens in
+Python, and there is no fallback: if the library is not built, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import c_double, c_float, c_int, c_int32, c_int64, c_void_p, POINTER
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libagents.so")
+
+AGENTS_OK = 0
+AGENTS_EINVAL = -1
+AGENTS_ECUDA = -2
+AGENTS_ENOMEM = -3
+AGENTS_ETIMEOUT = -4
+AGENTS_EDIVERGED = -5
+AGENTS_ESTATE = -6
+
+_NAMES = {0: "AGENTS_OK", -1: "AGENTS_EINVAL", -2: "AGENTS_ECUDA", -3: "AGENTS_ENOMEM",
+          -4: "AGENTS_ETIMEOUT", -5: "AGENTS_EDIVERGED", -6: "AGENTS_ESTATE"}
+
+
+class AgentsError(RuntimeError):
+    def __init__(self, code: int, func: str, message: str):
+        super().__init__(f"{func} -> {_NAMES.get(code, code)}: {message}")
+        self.code = code
+
+
+class agents_params(ctypes.Structure):
+    _fields_ = [("height", c_int32), ("width", c_int32), ("channels", c_int32),
+                ("radius", c_int32), ("nsteps", c_int32), ("dt", c_double),
+                ("alpha", c_double), ("rho", c_double), ("gamma", c_double),
+                ("eps_lo", c_double * 2), ("eps_hi", c_double * 2),
+                ("norm_mode", c_int32), ("tv_mode", c_int32), ("traj_mode", c_int32)]
+
+
+class agents_solve_opts(ctypes.Structure):
+    _fields_ = [("k_out", c_int32), ("k_in", c_int32), ("max_ls", c_int32),
+                ("sigma0", c_double), ("ls_b", c_double), ("ls_c", c_double), ("tol", c_double)]
+
+
+class agents_solve_info(ctypes.Structure):
+    _fields_ = [("outer_done", c_int32), ("inner_done", c_int32), ("trials", c_int32),
+                ("stalls", c_int32), ("stationary", c_int32),
+                ("forward_steps", c_int64), ("adjoint_steps", c_int64),
+                ("tv_sweeps", c_int64), ("final_res", c_double), ("final_obj", c_double),
+                ("final_gap", c_double), ("final_sigma", c_double), ("kernel_launches", c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class agents_iter_record(ctypes.Structure):
+    _fields_ = [("outer", c_int32), ("trials", c_int32), ("status", c_int32),
+                ("reserved", c_int32), ("L0", c_double), ("L", c_double),
+                ("gnorm2", c_double), ("tau", c_double)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGNATURES = {
+    "agents_default_params": (None, [POINTER(agents_params), c_int32, c_int32, c_int32, c_int32, c_int32]),
+    "agents_default_solve_opts": (None, [POINTER(agents_solve_opts)]),
+    "agents_init": (c_int, [POINTER(agents_params), c_void_p, c_void_p, POINTER(c_void_p)]),
+    "agents_set_image": (c_int, [c_void_p, c_void_p]),
+    "agents_destroy": (c_int, [c_void_p]),
+    "agents_last_error": (ctypes.c_char_p, [c_void_p]),
+    "agents_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    "agents_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "agents_objective": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pd_tv_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "alm_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "agents_labels": (c_int, [c_void_p, c_void_p, c_float, c_void_p, c_void_p]),
+    "agents_solve_log": (c_int, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
+    "solve": (c_int, [c_void_p, POINTER(agents_solve_opts), c_void_p, c_void_p, c_void_p,
+                      c_void_p, c_void_p, POINTER(agents_solve_info)]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_2510_16154_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x, dtype=None):
+    """Raw address of a torch tensor / numpy array / int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):          # torch.Tensor
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if dtype is not None and str(x.dtype).split(".")[-1] != dtype:
+            raise TypeError(f"expected {dtype}, got {x.dtype}")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):            # numpy.ndarray
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if dtype is not None and x.dtype.name != dtype:
+            raise TypeError(f"expected {dtype}, got {x.dtype}")
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x).__name__} as a pointer")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream           # torch.cuda.Stream
+
+
+def _check(status: int, func: str, ctx=None):
+    if status != AGENTS_OK:
+        msg = load().agents_last_error(ctx)
+        raise AgentsError(status, func, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------- entry points
+
+def agents_default_params(height, width, channels, radius, nsteps) -> agents_params:
+    p = agents_params()
+    load().agents_default_params(ctypes.byref(p), height, width, channels, radius, nsteps)
+    return p
+
+
+def agents_default_solve_opts() -> agents_solve_opts:
+    o = agents_solve_opts()
+    load().agents_default_solve_opts(ctypes.byref(o))
+    return o
+
+
+def agents_init(params: agents_params, c0, stream=None) -> c_void_p:
+    ctx = c_void_p()
+    _check(load().agents_init(ctypes.byref(params), _ptr(c0, "float32"), _stream(stream),
+                              ctypes.byref(ctx)), "agents_init")
+    return ctx
+
+
+def agents_set_image(ctx, c0):
+    _check(load().agents_set_image(ctx, _ptr(c0, "float32")), "agents_set_image", ctx)
+
+
+def agents_destroy(ctx):
+    _check(load().agents_destroy(ctx), "agents_destroy")
+
+
+def agents_last_error(ctx=None) -> str:
+    msg = load().agents_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def agents_forward(ctx, eps, cT=None, store=True):
+    _check(load().agents_forward(ctx, _ptr(eps, "float64"), _ptr(cT, "float32"), int(bool(store))),
+           "agents_forward", ctx)
+
+
+def agents_adjoint(ctx, eps, v, mu, D_out, obj_out=None, lambda0=None):
+    _check(load().agents_adjoint(ctx, _ptr(eps, "float64"), _ptr(v, "float32"),
+                                 _ptr(mu, "float32"), _ptr(D_out, "float64"),
+                                 _ptr(obj_out, "float64"), _ptr(lambda0, "float32")),
+           "agents_adjoint", ctx)
+
+
+def agents_objective(ctx, c, v, mu, obj_out=None, lam=None):
+    _check(load().agents_objective(ctx, _ptr(c, "float32"), _ptr(v, "float32"),
+                                   _ptr(mu, "float32"), _ptr(obj_out, "float64"),
+                                   _ptr(lam, "float32")), "agents_objective", ctx)
+
+
+def pd_tv_step(ctx, c, mu, v):
+    _check(load().pd_tv_step(ctx, _ptr(c, "float32"), _ptr(mu, "float32"), _ptr(v, "float32")),
+           "pd_tv_step", ctx)
+
+
+def alm_update(ctx, c, c_prev, v, v_prev, mu, stats=None):
+    _check(load().alm_update(ctx, _ptr(c, "float32"), _ptr(c_prev, "float32"),
+                             _ptr(v, "float32"), _ptr(v_prev, "float32"), _ptr(mu, "float32"),
+                             _ptr(stats, "float64")), "alm_update", ctx)
+
+
+def agents_labels(ctx, c, threshold, labels_out) -> int:
+    count = c_int32(0)
+    _check(load().agents_labels(ctx, _ptr(c, "float32"), c_float(threshold),
+                                _ptr(labels_out, "int32"), ctypes.byref(count)),
+           "agents_labels", ctx)
+    return count.value
+
+
+def solve(ctx, opts: agents_solve_opts, eps_io, mu_io, v_out=None, c_out=None,
+          labels_out=None) -> agents_solve_info:
+    info = agents_solve_info()
+    _check(load().solve(ctx, ctypes.byref(opts), _ptr(eps_io, "float64"), _ptr(mu_io, "float32"),
+                        _ptr(v_out, "float32"), _ptr(c_out, "float32"),
+                        _ptr(labels_out, "int32"), ctypes.byref(info)), "solve", ctx)
+    return info
+
+
+def agents_solve_log(ctx):
+    """Per-DAL-iteration records of the last solve() as a list of dicts."""
+    n = c_int32(0)
+    _check(load().agents_solve_log(ctx, None, 0, ctypes.byref(n)), "agents_solve_log", ctx)
+    buf = (agents_iter_record * max(n.value, 1))()
+    _check(load().agents_solve_log(ctx, buf, n.value, ctypes.byref(n)), "agents_solve_log", ctx)
+    return [{f: getattr(buf[i], f) for f, _ in agents_iter_record._fields_ if f != "reserved"}
+            for i in range(n.value)]
+
+
+class Context:
+    """Owns one ``agents_ctx`` (destroyed on close / garbage collection)."""
+
+    def __init__(self, params: agents_params, c0, stream=None):
+        self.params = params
+        self.handle = agents_init(params, c0, stream)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            agents_destroy(self.handle)
+        self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,782 @@
+// C ABI of the agent-based optimal-control image solver: context and workspace
+// management, the per-sweep entry points, and solve() -- Algorithm 2 (ADMM) with
+// Algorithm 1 (direct-adjoint loop with projected two-way Armijo) as its eps-step.
+//
+// Host code drives the iteration: the Armijo accept/reject test needs one float64
+// objective per trial on the host, the only host/device round trip of a DAL iteration.
+// Everything else (Euler steps, adjoint steps, control projection, reductions) runs in
+// the kernels declared in kernels.h, stream-ordered on the context's stream.
+#include "agents.h"
+#include "kernels.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace agents;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct agents_ctx {
+  agents_params p{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+
+  int N = 0, C = 0, T = 0;
+  size_t nc = 0, nv = 0;  // floats per colour field, per TV field
+  SweepGeom sg{};
+  TvGeom tg{};
+  double M = 1.0;
+
+  // colour fields
+  float* c0 = nullptr;       // input image c^0
+  float* cT = nullptr;       // c^T of the last stored forward
+  float* work[2] = {nullptr, nullptr};
+  float* lam[2] = {nullptr, nullptr};
+  float* traj = nullptr;     // stored states (mode 0: c^1..c^{T-1}; mode k: checkpoints)
+  float* seg = nullptr;      // mode k: recomputed states of one checkpoint segment
+  int ckpt_every = 0;        // 0: full store; k: checkpoint every k steps
+  int nckpt = 0;
+
+  // control and reductions
+  double* d_eps = nullptr;       // [T][2]
+  double* d_trial[2] = {nullptr, nullptr};
+  double* d_D = nullptr;         // [T][2]
+  double* d_lohi = nullptr;      // [4]
+  double* d_part_adj = nullptr;  // [T][nb_adj][2]
+  double* d_part_tv = nullptr;   // [nb_tv][5]
+  double* d_scal = nullptr;      // [16] small device results
+  double* h_scal = nullptr;      // pinned [16]
+  int nb_adj = 0, nb_tv = 0;
+
+  // labels
+  int32_t* d_labels = nullptr;
+  int32_t* d_lstat = nullptr;    // [2] = {count, status}
+
+  // stored-trajectory bookkeeping
+  bool stored = false;
+  std::vector<double> stored_eps;
+
+  // solve workspaces (allocated on first solve)
+  float *s_c = nullptr, *s_cn = nullptr, *s_v = nullptr, *s_vn = nullptr, *s_mu = nullptr;
+  float* s_trial_c = nullptr;
+
+  int64_t launches = 0;           // kernels launched by this context (for accounting)
+  std::vector<agents_iter_record> log;  // per-DAL-iteration records of the last solve()
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(agents_ctx* ctx, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else g_init_error = buf;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? AGENTS_ENOMEM : AGENTS_ECUDA, \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define TRY(expr)              \
+  do {                         \
+    int st_ = (expr);          \
+    if (st_ != AGENTS_OK) return st_; \
+  } while (0)
+
+template <class T>
+int dalloc(agents_ctx* ctx, T** out, size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, AGENTS_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                cudaGetErrorString(e));
+  }
+  ctx->allocs.push_back(p);
+  *out = static_cast<T*>(p);
+  return AGENTS_OK;
+}
+
+int validate(const agents_params* p) {
+  if (!p) return fail(nullptr, AGENTS_EINVAL, "params is NULL");
+  if (p->height < 1 || p->width < 1 || p->channels < 1)
+    return fail(nullptr, AGENTS_EINVAL, "height, width and channels must be >= 1");
+  if ((int64_t)p->height * p->width > (int64_t)1 << 30)
+    return fail(nullptr, AGENTS_EINVAL, "image too large (more than 2^30 pixels)");
+  if (p->channels > 64) return fail(nullptr, AGENTS_EINVAL, "channels must be <= 64");
+  if (p->radius < 1) return fail(nullptr, AGENTS_EINVAL, "radius must be >= 1");
+  if (p->nsteps < 1) return fail(nullptr, AGENTS_EINVAL, "nsteps must be >= 1");
+  if (!(p->dt > 0) || !(p->alpha > 0) || !(p->rho > 0) || !(p->gamma > 0))
+    return fail(nullptr, AGENTS_EINVAL, "dt, alpha, rho and gamma must be > 0");
+  for (int k = 0; k < 2; ++k)
+    if (!(p->eps_lo[k] >= 0) || !(p->eps_lo[k] <= p->eps_hi[k]) || !std::isfinite(p->eps_hi[k]))
+      return fail(nullptr, AGENTS_EINVAL, "need 0 <= eps_lo <= eps_hi < inf");
+  if (p->norm_mode != 0 && p->norm_mode != 1)
+    return fail(nullptr, AGENTS_EINVAL, "norm_mode must be 0 or 1");
+  if (p->tv_mode != 0 && p->tv_mode != 1) return fail(nullptr, AGENTS_EINVAL, "tv_mode must be 0 or 1");
+  if (p->traj_mode < 0) return fail(nullptr, AGENTS_EINVAL, "traj_mode must be >= 0");
+  return AGENTS_OK;
+}
+
+// Copy n bytes from src (host or device) into device dst on the context stream.
+int to_device(agents_ctx* ctx, void* dst, const void* src, size_t n) {
+  CK(cudaMemcpyAsync(dst, src, n, is_device_ptr(src) ? cudaMemcpyDeviceToDevice
+                                                      : cudaMemcpyHostToDevice,
+                     ctx->stream));
+  return AGENTS_OK;
+}
+
+// Copy n bytes from device src into dst (host or device); host destinations are
+// complete when this returns.
+int from_device(agents_ctx* ctx, void* dst, const void* src, size_t n) {
+  if (is_device_ptr(dst)) {
+    CK(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, ctx->stream));
+  } else {
+    CK(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return AGENTS_OK;
+}
+
+int check_aligned(agents_ctx* ctx, const void* p, const char* name) {
+  if (p && (reinterpret_cast<uintptr_t>(p) & 15u))
+    return fail(ctx, AGENTS_EINVAL, "%s must be 16-byte aligned", name);
+  return AGENTS_OK;
+}
+
+int need(agents_ctx* ctx, const void* p, const char* name) {
+  if (!p) return fail(ctx, AGENTS_EINVAL, "%s is NULL", name);
+  return check_aligned(ctx, p, name);
+}
+
+// ------------------------------------------------------------------ sweeps
+// Pointer to stored state c^n (0 <= n < T) for the full-store mode.
+const float* full_state(agents_ctx* ctx, int n) {
+  return n == 0 ? ctx->c0 : ctx->traj + (size_t)(n - 1) * ctx->nc;
+}
+
+// Forward sweep under the device control d_eps; c^T goes to dst_T.  With store, the
+// states the adjoint needs are kept (all of them, or every k-th).
+int forward_sweep(agents_ctx* ctx, const double* d_eps, float* dst_T, bool store) {
+  const int T = ctx->T;
+  const float* cur = ctx->c0;
+  int wi = 0;
+  for (int n = 0; n < T; ++n) {
+    float* dst;
+    if (n == T - 1) {
+      dst = dst_T;
+    } else if (store && ctx->ckpt_every == 0) {
+      dst = ctx->traj + (size_t)n * ctx->nc;
+    } else if (store && (n + 1) % ctx->ckpt_every == 0) {
+      dst = ctx->traj + (size_t)((n + 1) / ctx->ckpt_every - 1) * ctx->nc;
+    } else {
+      dst = ctx->work[wi];
+      if (dst == cur) dst = ctx->work[wi ^ 1];
+      wi = (dst == ctx->work[0]) ? 1 : 0;
+    }
+    CK(launch_forward_step(cur, dst, d_eps + 2 * n, ctx->sg, ctx->stream));
+    ++ctx->launches;
+    cur = dst;
+  }
+  return AGENTS_OK;
+}
+
+// L~(c, v, mu) into d_scal[slot] (device); lam (optional) = -dL~/dc.
+int objective(agents_ctx* ctx, const float* c, const float* v, const float* mu, float* lam,
+              int slot) {
+  CK(launch_objective(c, ctx->c0, v, mu, lam, ctx->d_part_tv, ctx->tg, ctx->stream));
+  CK(launch_reduce_rows(ctx->d_part_tv, ctx->nb_tv, 1, 1, 1.0, ctx->d_scal + slot, ctx->stream));
+  ctx->launches += 2;
+  return AGENTS_OK;
+}
+
+int fetch_scalar(agents_ctx* ctx, int slot, double* out) {
+  CK(cudaMemcpyAsync(ctx->h_scal + slot, ctx->d_scal + slot, sizeof(double),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *out = ctx->h_scal[slot];
+  return AGENTS_OK;
+}
+
+// Reverse sweep from lambda^T = -dL~/dc(c^T); D^n (times 1/(2M)) into ctx->d_D.
+// Returns the final lambda^0 buffer in *lam_out.
+int adjoint_sweep(agents_ctx* ctx, const double* d_eps, const float* v, const float* mu,
+                  int obj_slot, float** lam_out) {
+  const int T = ctx->T;
+  TRY(objective(ctx, ctx->cT, v, mu, ctx->lam[0], obj_slot));
+  int li = 0;
+  const size_t pstride = (size_t)ctx->nb_adj * 2;
+  auto step = [&](int n, const float* cn) -> int {
+    CK(launch_adjoint_step(cn, ctx->lam[li], ctx->lam[li ^ 1], d_eps + 2 * n,
+                           ctx->d_part_adj + (size_t)n * pstride, ctx->sg, ctx->stream));
+    ++ctx->launches;
+    li ^= 1;
+    return AGENTS_OK;
+  };
+  if (ctx->ckpt_every == 0) {
+    for (int n = T - 1; n >= 0; --n) TRY(step(n, full_state(ctx, n)));
+  } else {
+    const int k = ctx->ckpt_every;
+    const int nseg = (T + k - 1) / k;
+    for (int m = nseg - 1; m >= 0; --m) {
+      const int n0 = m * k, len = std::min(k, T - n0);
+      const float* base = m == 0 ? ctx->c0 : ctx->traj + (size_t)(m - 1) * ctx->nc;
+      // recompute c^{n0+1} .. c^{n0+len-1} into seg[0..len-2]
+      const float* cur = base;
+      for (int i = 1; i < len; ++i) {
+        float* dst = ctx->seg + (size_t)(i - 1) * ctx->nc;
+        CK(launch_forward_step(cur, dst, d_eps + 2 * (n0 + i - 1), ctx->sg, ctx->stream));
+        ++ctx->launches;
+        cur = dst;
+      }
+      for (int i = len - 1; i >= 0; --i) {
+        const float* cn = i == 0 ? base : ctx->seg + (size_t)(i - 1) * ctx->nc;
+        TRY(step(n0 + i, cn));
+      }
+    }
+  }
+  CK(launch_reduce_rows(ctx->d_part_adj, ctx->nb_adj, 2, T, 1.0 / (2.0 * ctx->M), ctx->d_D,
+                        ctx->stream));
+  ++ctx->launches;
+  *lam_out = ctx->lam[li];
+  return AGENTS_OK;
+}
+
+int alm(agents_ctx* ctx, const float* c, const float* c_prev, const float* v,
+        const float* v_prev, float* mu, double* h_stats /*host[5]*/, double* d_stats) {
+  CK(launch_alm_update(c, c_prev, ctx->c0, v, v_prev, mu, ctx->d_part_tv, ctx->tg, ctx->stream));
+  CK(launch_reduce_rows(ctx->d_part_tv, ctx->nb_tv, 5, 1, 1.0, ctx->d_scal + 8, ctx->stream));
+  ctx->launches += 2;
+  if (d_stats) {
+    CK(launch_alm_finalize(ctx->d_scal + 8, d_stats, ctx->p.rho, ctx->p.gamma, ctx->tg.cell,
+                           ctx->stream));
+    ++ctx->launches;
+  }
+  if (h_stats) {
+    double raw[5];
+    CK(cudaMemcpyAsync(ctx->h_scal + 8, ctx->d_scal + 8, 5 * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::memcpy(raw, ctx->h_scal + 8, sizeof(raw));
+    const double cell = ctx->tg.cell;
+    h_stats[0] = std::sqrt(raw[0]);
+    h_stats[1] = ctx->p.rho * std::sqrt(raw[1]);
+    h_stats[2] = ctx->p.gamma * cell * raw[0];
+    h_stats[3] = raw[3] > 0 ? std::sqrt(raw[2] / raw[3]) : 0.0;
+    h_stats[4] = cell * raw[4];
+  }
+  return AGENTS_OK;
+}
+
+int ensure_solve_buffers(agents_ctx* ctx) {
+  if (ctx->s_c) return AGENTS_OK;
+  TRY(dalloc(ctx, &ctx->s_c, ctx->nc));
+  TRY(dalloc(ctx, &ctx->s_cn, ctx->nc));
+  TRY(dalloc(ctx, &ctx->s_trial_c, ctx->nc));
+  TRY(dalloc(ctx, &ctx->s_v, ctx->nv));
+  TRY(dalloc(ctx, &ctx->s_vn, ctx->nv));
+  TRY(dalloc(ctx, &ctx->s_mu, ctx->nv));
+  return AGENTS_OK;
+}
+
+int read_control(agents_ctx* ctx, const double* eps, std::vector<double>& host) {
+  host.resize(2 * (size_t)ctx->T);
+  if (is_device_ptr(eps)) {
+    CK(cudaMemcpyAsync(host.data(), eps, host.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else {
+    std::memcpy(host.data(), eps, host.size() * sizeof(double));
+  }
+  for (double e : host)
+    if (!std::isfinite(e)) return fail(ctx, AGENTS_EINVAL, "control contains NaN/Inf");
+  return AGENTS_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void agents_default_params(agents_params* p, int32_t height, int32_t width, int32_t channels,
+                           int32_t radius, int32_t nsteps) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->height = height;
+  p->width = width;
+  p->channels = channels;
+  p->radius = radius;
+  p->nsteps = nsteps;
+  p->dt = 0.25;
+  p->alpha = 3000.0;
+  p->rho = 1e-2;
+  p->gamma = 1e-2;
+  p->eps_lo[0] = p->eps_lo[1] = 2.0;
+  p->eps_hi[0] = p->eps_hi[1] = 1100.0;
+  p->norm_mode = 0;
+  p->tv_mode = 0;
+  p->traj_mode = 0;
+}
+
+void agents_default_solve_opts(agents_solve_opts* o) {
+  if (!o) return;
+  o->k_out = 10;
+  o->k_in = 30;
+  o->max_ls = 30;
+  o->sigma0 = 1.0;
+  o->ls_b = 0.5;
+  o->ls_c = 1e-4;
+  o->tol = 0.0;
+}
+
+const char* agents_last_error(const agents_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+int agents_destroy(agents_ctx* ctx) {
+  if (!ctx) return AGENTS_OK;
+  DeviceGuard dg(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+  delete ctx;
+  return AGENTS_OK;
+}
+
+int agents_init(const agents_params* p, const float* c0, void* cuda_stream, agents_ctx** out) {
+  g_init_error.clear();
+  if (!out) return fail(nullptr, AGENTS_EINVAL, "out is NULL");
+  *out = nullptr;
+  TRY(validate(p));
+  if (!c0) return fail(nullptr, AGENTS_EINVAL, "c0 is NULL");
+  agents_ctx* ctx = new (std::nothrow) agents_ctx();
+  if (!ctx) return fail(nullptr, AGENTS_ENOMEM, "host allocation failed");
+  ctx->p = *p;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&ctx->device);
+  const int H = p->height, W = p->width, C = p->channels, T = p->nsteps;
+  ctx->N = H * W;
+  ctx->C = C;
+  ctx->T = T;
+  ctx->nc = (size_t)ctx->N * C;
+  ctx->nv = ctx->nc * 2;
+  ctx->M = p->norm_mode == 0 ? (double)(2 * p->radius + 1) * (2 * p->radius + 1) : (double)ctx->N;
+  ctx->sg = SweepGeom{H, W, C, p->radius, (float)(1.0 / ((double)W * W)),
+                      (float)(1.0 / ((double)H * H)), (float)(p->dt / ctx->M)};
+  ctx->tg = TvGeom{H, W, C, (float)(0.5 * W), (float)(0.5 * H), (float)p->rho,
+                   (float)(1.0 / p->rho), (float)p->alpha, (float)p->gamma,
+                   1.0 / ((double)W * (double)H), p->tv_mode};
+  ctx->ckpt_every = p->traj_mode >= T ? 0 : p->traj_mode;
+  ctx->nb_adj = adjoint_num_blocks(ctx->sg);
+  ctx->nb_tv = tv_num_blocks(ctx->tg);
+
+  auto bail = [&](int st) {
+    std::string msg = ctx->err;
+    agents_destroy(ctx);
+    g_init_error = msg;
+    return st;
+  };
+  int st = AGENTS_OK;
+#define INIT_TRY(expr)                \
+  do {                                \
+    st = (expr);                      \
+    if (st != AGENTS_OK) return bail(st); \
+  } while (0)
+  INIT_TRY(dalloc(ctx, &ctx->c0, ctx->nc));
+  INIT_TRY(dalloc(ctx, &ctx->cT, ctx->nc));
+  INIT_TRY(dalloc(ctx, &ctx->work[0], ctx->nc));
+  INIT_TRY(dalloc(ctx, &ctx->work[1], ctx->nc));
+  INIT_TRY(dalloc(ctx, &ctx->lam[0], ctx->nc));
+  INIT_TRY(dalloc(ctx, &ctx->lam[1], ctx->nc));
+  if (ctx->ckpt_every == 0) {
+    ctx->nckpt = T - 1;
+    INIT_TRY(dalloc(ctx, &ctx->traj, ctx->nc * (size_t)std::max(T - 1, 1)));
+  } else {
+    const int k = ctx->ckpt_every;
+    ctx->nckpt = (T - 1) / k;  // states k, 2k, ... <= T-1
+    INIT_TRY(dalloc(ctx, &ctx->traj, ctx->nc * (size_t)std::max(ctx->nckpt, 1)));
+    INIT_TRY(dalloc(ctx, &ctx->seg, ctx->nc * (size_t)std::max(k - 1, 1)));
+  }
+  INIT_TRY(dalloc(ctx, &ctx->d_eps, 2 * (size_t)T));
+  INIT_TRY(dalloc(ctx, &ctx->d_trial[0], 2 * (size_t)T));
+  INIT_TRY(dalloc(ctx, &ctx->d_trial[1], 2 * (size_t)T));
+  INIT_TRY(dalloc(ctx, &ctx->d_D, 2 * (size_t)T));
+  INIT_TRY(dalloc(ctx, &ctx->d_lohi, 4));
+  INIT_TRY(dalloc(ctx, &ctx->d_part_adj, (size_t)T * ctx->nb_adj * 2));
+  INIT_TRY(dalloc(ctx, &ctx->d_part_tv, (size_t)ctx->nb_tv * 5));
+  INIT_TRY(dalloc(ctx, &ctx->d_scal, 16));
+  INIT_TRY(dalloc(ctx, &ctx->d_labels, (size_t)ctx->N));
+  INIT_TRY(dalloc(ctx, &ctx->d_lstat, 2));
+  {
+    cudaError_t e = cudaMallocHost(&ctx->h_scal, 16 * sizeof(double));
+    if (e != cudaSuccess) {
+      ctx->err = std::string("cudaMallocHost failed: ") + cudaGetErrorString(e);
+      return bail(AGENTS_ENOMEM);
+    }
+  }
+  const double lohi[4] = {p->eps_lo[0], p->eps_lo[1], p->eps_hi[0], p->eps_hi[1]};
+  {
+    cudaError_t e = cudaMemcpyAsync(ctx->d_lohi, lohi, sizeof(lohi), cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e != cudaSuccess) {
+      ctx->err = std::string("copy of the box failed: ") + cudaGetErrorString(e);
+      return bail(AGENTS_ECUDA);
+    }
+  }
+  INIT_TRY(to_device(ctx, ctx->c0, c0, ctx->nc * sizeof(float)));
+  {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      ctx->err = std::string("init synchronisation failed: ") + cudaGetErrorString(e);
+      return bail(AGENTS_ECUDA);
+    }
+  }
+#undef INIT_TRY
+  *out = ctx;
+  return AGENTS_OK;
+}
+
+int agents_set_image(agents_ctx* ctx, const float* c0) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  if (!c0) return fail(ctx, AGENTS_EINVAL, "c0 is NULL");
+  DeviceGuard dg(ctx->device);
+  ctx->stored = false;
+  return to_device(ctx, ctx->c0, c0, ctx->nc * sizeof(float));
+}
+
+int agents_forward(agents_ctx* ctx, const double* eps, float* cT_dev, int store) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  if (!eps) return fail(ctx, AGENTS_EINVAL, "eps is NULL");
+  TRY(check_aligned(ctx, cT_dev, "cT_dev"));
+  DeviceGuard dg(ctx->device);
+  std::vector<double> host;
+  TRY(read_control(ctx, eps, host));
+  CK(cudaMemcpyAsync(ctx->d_eps, host.data(), host.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  TRY(forward_sweep(ctx, ctx->d_eps, ctx->cT, store != 0));
+  if (cT_dev) CK(cudaMemcpyAsync(cT_dev, ctx->cT, ctx->nc * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+  if (store) {
+    ctx->stored = true;
+    ctx->stored_eps = host;
+  } else {
+    ctx->stored = false;  // cT and the work buffers were overwritten
+  }
+  CK(cudaStreamSynchronize(ctx->stream));  // host control buffer goes out of scope
+  return AGENTS_OK;
+}
+
+int agents_adjoint(agents_ctx* ctx, const double* eps, const float* v_dev, const float* mu_dev,
+                   double* D_out, double* obj_out, float* lambda0_dev) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  if (!eps || !D_out) return fail(ctx, AGENTS_EINVAL, "eps and D_out must not be NULL");
+  TRY(need(ctx, v_dev, "v_dev"));
+  TRY(need(ctx, mu_dev, "mu_dev"));
+  TRY(check_aligned(ctx, lambda0_dev, "lambda0_dev"));
+  DeviceGuard dg(ctx->device);
+  std::vector<double> host;
+  TRY(read_control(ctx, eps, host));
+  if (!ctx->stored || host != ctx->stored_eps)
+    return fail(ctx, AGENTS_ESTATE, "agents_adjoint needs a preceding agents_forward(store=1) "
+                                    "with the same control");
+  float* lam0 = nullptr;
+  TRY(adjoint_sweep(ctx, ctx->d_eps, v_dev, mu_dev, 0, &lam0));
+  if (lambda0_dev) CK(cudaMemcpyAsync(lambda0_dev, lam0, ctx->nc * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+  if (obj_out) TRY(from_device(ctx, obj_out, ctx->d_scal + 0, sizeof(double)));
+  TRY(from_device(ctx, D_out, ctx->d_D, 2 * (size_t)ctx->T * sizeof(double)));
+  return AGENTS_OK;
+}
+
+int agents_objective(agents_ctx* ctx, const float* c_dev, const float* v_dev,
+                     const float* mu_dev, double* obj_out, float* lambda_dev) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  TRY(need(ctx, c_dev, "c_dev"));
+  TRY(need(ctx, v_dev, "v_dev"));
+  TRY(need(ctx, mu_dev, "mu_dev"));
+  TRY(check_aligned(ctx, lambda_dev, "lambda_dev"));
+  DeviceGuard dg(ctx->device);
+  TRY(objective(ctx, c_dev, v_dev, mu_dev, lambda_dev, 1));
+  if (obj_out) TRY(from_device(ctx, obj_out, ctx->d_scal + 1, sizeof(double)));
+  return AGENTS_OK;
+}
+
+int pd_tv_step(agents_ctx* ctx, const float* c_dev, const float* mu_dev, float* v_dev) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  TRY(need(ctx, c_dev, "c_dev"));
+  TRY(need(ctx, mu_dev, "mu_dev"));
+  TRY(need(ctx, v_dev, "v_dev"));
+  DeviceGuard dg(ctx->device);
+  CK(launch_pd_tv_step(c_dev, mu_dev, v_dev, ctx->tg, ctx->stream));
+  return AGENTS_OK;
+}
+
+int alm_update(agents_ctx* ctx, const float* c_dev, const float* c_prev_dev, const float* v_dev,
+               const float* v_prev_dev, float* mu_dev, double* stats) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  TRY(need(ctx, c_dev, "c_dev"));
+  TRY(need(ctx, v_dev, "v_dev"));
+  TRY(need(ctx, mu_dev, "mu_dev"));
+  TRY(check_aligned(ctx, c_prev_dev, "c_prev_dev"));
+  TRY(check_aligned(ctx, v_prev_dev, "v_prev_dev"));
+  DeviceGuard dg(ctx->device);
+  double* d_stats = (stats && is_device_ptr(stats)) ? stats : nullptr;
+  double* h_stats = (stats && !d_stats) ? stats : nullptr;
+  return alm(ctx, c_dev, c_prev_dev, v_dev, v_prev_dev, mu_dev, h_stats, d_stats);
+}
+
+int agents_solve_log(const agents_ctx* ctx, agents_iter_record* out, int32_t capacity,
+                     int32_t* count) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  if (count) *count = (int32_t)ctx->log.size();
+  if (out && capacity > 0) {
+    const size_t n = std::min((size_t)capacity, ctx->log.size());
+    std::memcpy(out, ctx->log.data(), n * sizeof(agents_iter_record));
+  }
+  return AGENTS_OK;
+}
+
+int agents_labels(agents_ctx* ctx, const float* c_dev, float threshold, int32_t* labels_out,
+                  int32_t* count_out) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  TRY(need(ctx, c_dev, "c_dev"));
+  if (!labels_out) return fail(ctx, AGENTS_EINVAL, "labels_out is NULL");
+  DeviceGuard dg(ctx->device);
+  CK(launch_labels(c_dev, ctx->p.height, ctx->p.width, ctx->C, threshold, ctx->d_labels,
+                   ctx->d_lstat, ctx->d_lstat + 1, ctx->stream));
+  int32_t hs[2];
+  CK(cudaMemcpyAsync(hs, ctx->d_lstat, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hs[1] != 0) return fail(ctx, AGENTS_ETIMEOUT, "label union-find exceeded its loop bound");
+  if (count_out) *count_out = hs[0];
+  TRY(from_device(ctx, labels_out, ctx->d_labels, (size_t)ctx->N * sizeof(int32_t)));
+  return AGENTS_OK;
+}
+
+int solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float* mu_io,
+          float* v_out, float* c_out, int32_t* labels_out, agents_solve_info* info) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  if (!opts || !eps_io || !mu_io) return fail(ctx, AGENTS_EINVAL, "opts, eps_io, mu_io must not be NULL");
+  const agents_solve_opts o = *opts;
+  if (o.k_out < 0 || o.k_in < 0 || o.max_ls < 1 || !(o.sigma0 > 0) || !(o.ls_b > 0 && o.ls_b < 1) ||
+      !(o.ls_c > 0 && o.ls_c < 1) || !(o.tol >= 0))
+    return fail(ctx, AGENTS_EINVAL, "invalid solve options");
+  DeviceGuard dg(ctx->device);
+  TRY(ensure_solve_buffers(ctx));
+  const int64_t launches0 = ctx->launches;
+  const int T = ctx->T;
+  const double dt = ctx->p.dt;
+  agents_solve_info inf{};
+  auto count_fwd = [&]() { inf.forward_steps += T; };
+
+  std::vector<double> eps_h;
+  TRY(read_control(ctx, eps_io, eps_h));
+  ctx->log.clear();
+  const double lo[2] = {ctx->p.eps_lo[0], ctx->p.eps_lo[1]};
+  const double hi[2] = {ctx->p.eps_hi[0], ctx->p.eps_hi[1]};
+  CK(cudaMemcpyAsync(ctx->d_eps, eps_h.data(), eps_h.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  TRY(to_device(ctx, ctx->s_mu, mu_io, ctx->nv * sizeof(float)));
+  ctx->stored = false;
+
+  double sigma = o.sigma0;
+  float *c = ctx->s_c, *cn = ctx->s_cn, *v = ctx->s_v, *vn = ctx->s_vn, *mu = ctx->s_mu;
+  // c^(0) = c(T; eps^(0)),  v^(0) = argmin_v L(c^(0), v, mu^(0))
+  TRY(forward_sweep(ctx, ctx->d_eps, c, false));
+  count_fwd();
+  CK(launch_pd_tv_step(c, mu, v, ctx->tg, ctx->stream));
+  ++ctx->launches;
+  TRY(objective(ctx, c, v, mu, nullptr, 2));
+  inf.tv_sweeps += 2;
+  double L_prev;
+  TRY(fetch_scalar(ctx, 2, &L_prev));
+  int status = AGENTS_OK;
+  std::vector<double> Dh(2 * (size_t)T);
+
+  for (int j = 1; j <= o.k_out && status == AGENTS_OK; ++j) {
+    // ---- eps-step: k_in iterations of Algorithm 1 on L~(c(T; eps), v, mu)
+    for (int it = 0; it < o.k_in; ++it) {
+      TRY(forward_sweep(ctx, ctx->d_eps, ctx->cT, true));
+      count_fwd();
+      float* lam0 = nullptr;
+      TRY(adjoint_sweep(ctx, ctx->d_eps, v, mu, 0, &lam0));
+      inf.adjoint_steps += T;
+      inf.tv_sweeps += 1;
+      if (ctx->ckpt_every) inf.forward_steps += T - 1 - ctx->nckpt;
+      double L0;
+      TRY(fetch_scalar(ctx, 0, &L0));
+      CK(cudaMemcpyAsync(Dh.data(), ctx->d_D, Dh.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+      CK(cudaMemcpyAsync(eps_h.data(), ctx->d_eps, eps_h.size() * sizeof(double),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      ++inf.inner_done;
+      agents_iter_record rec{j, 0, 0, 0, L0, L0, 0.0, 0.0};
+      if (!std::isfinite(L0)) { status = AGENTS_EDIVERGED; break; }
+      // Components the projection onto E does not block; |P D|^2 over those only.
+      double g2 = 0.0;
+      bool any_free = false;
+      for (size_t i = 0; i < Dh.size(); ++i) {
+        const int k = (int)(i & 1);
+        const double d = Dh[i], e = eps_h[i];
+        if (d != 0.0 && (e < hi[k] || d < 0.0) && (e > lo[k] || d > 0.0)) {
+          any_free = true;
+          g2 += d * d;
+        }
+      }
+      g2 *= dt;
+      rec.gnorm2 = g2;
+      if (!std::isfinite(g2)) { status = AGENTS_EDIVERGED; break; }
+      if (!any_free) {  // variational inequality holds: the control is stationary
+        ++inf.stationary;
+        rec.status = 2;
+        ctx->log.push_back(rec);
+        break;
+      }
+      int cur = 0, best = -1;
+      double best_tau = 0.0, best_L = L0;
+      auto trial = [&](double tau, bool& ok) -> int {
+        CK(launch_control_step(ctx->d_eps, ctx->d_D, tau, ctx->d_lohi, ctx->d_trial[cur], T,
+                               ctx->stream));
+        ++ctx->launches;
+        TRY(forward_sweep(ctx, ctx->d_trial[cur], ctx->s_trial_c, false));
+        count_fwd();
+        TRY(objective(ctx, ctx->s_trial_c, v, mu, nullptr, 1));
+        inf.tv_sweeps += 1;
+        ++inf.trials;
+        double L;
+        TRY(fetch_scalar(ctx, 1, &L));
+        if (!std::isfinite(L)) return AGENTS_EDIVERGED;
+        ok = (L < L0) && (L <= L0 - o.ls_c * tau * g2);
+        if (ok) {
+          best = cur;
+          best_tau = tau;
+          best_L = L;
+          cur ^= 1;  // keep the passing trial; write the next one into the other buffer
+        }
+        return AGENTS_OK;
+      };
+      double tau = sigma;
+      bool ok = false;
+      int ntr = 1;
+      int ts = trial(tau, ok);
+      if (ts != AGENTS_OK) { status = ts; break; }
+      if (ok) {
+        while (ntr < o.max_ls) {
+          tau = tau / o.ls_b;
+          ++ntr;
+          ts = trial(tau, ok);
+          if (ts != AGENTS_OK || !ok) break;
+        }
+      } else {
+        while (ntr < o.max_ls) {
+          tau = tau * o.ls_b;
+          ++ntr;
+          ts = trial(tau, ok);
+          if (ts != AGENTS_OK || ok) break;
+        }
+      }
+      if (ts != AGENTS_OK) { status = ts; break; }
+      rec.trials = ntr;
+      if (best < 0) {
+        ++inf.stalls;
+        rec.status = 1;
+        ctx->log.push_back(rec);
+        break;
+      }
+      rec.L = best_L;
+      rec.tau = best_tau;
+      ctx->log.push_back(rec);
+      CK(cudaMemcpyAsync(ctx->d_eps, ctx->d_trial[best], 2 * (size_t)T * sizeof(double),
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+      sigma = best_tau;
+    }
+    if (status != AGENTS_OK) break;
+    // ---- c^(j), v^(j), mu^(j)
+    TRY(forward_sweep(ctx, ctx->d_eps, cn, false));
+    count_fwd();
+    CK(launch_pd_tv_step(cn, mu, vn, ctx->tg, ctx->stream));
+    ++ctx->launches;
+    double st[5];
+    TRY(alm(ctx, cn, c, vn, v, mu, st, nullptr));
+    TRY(objective(ctx, cn, vn, mu, nullptr, 2));
+    inf.tv_sweeps += 3;
+    double L_new;
+    TRY(fetch_scalar(ctx, 2, &L_new));
+    std::swap(c, cn);
+    std::swap(v, vn);
+    inf.outer_done = j;
+    if (!std::isfinite(L_new) || !std::isfinite(st[0]) || !std::isfinite(st[1])) {
+      status = AGENTS_EDIVERGED;
+      break;
+    }
+    const double dL = L_prev != 0.0 ? std::fabs(L_new - L_prev) / std::fabs(L_prev) : 0.0;
+    inf.final_res = std::max(st[3], dL);
+    inf.final_obj = L_new;
+    inf.final_gap = st[2];
+    L_prev = L_new;
+    if (o.tol > 0.0 && inf.final_res < o.tol) break;
+  }
+  ctx->stored = false;
+  // outputs
+  TRY(from_device(ctx, eps_io, ctx->d_eps, 2 * (size_t)T * sizeof(double)));
+  TRY(from_device(ctx, mu_io, mu, ctx->nv * sizeof(float)));
+  if (v_out) TRY(from_device(ctx, v_out, v, ctx->nv * sizeof(float)));
+  if (c_out) TRY(from_device(ctx, c_out, c, ctx->nc * sizeof(float)));
+  if (labels_out) {
+    CK(launch_labels(c, ctx->p.height, ctx->p.width, ctx->C, 0.02f, ctx->d_labels, ctx->d_lstat,
+                     ctx->d_lstat + 1, ctx->stream));
+    ctx->launches += 3;
+    TRY(from_device(ctx, labels_out, ctx->d_labels, (size_t)ctx->N * sizeof(int32_t)));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  inf.final_sigma = sigma;
+  inf.kernel_launches = ctx->launches - launches0;
+  if (info) *info = inf;
+  if (status == AGENTS_EDIVERGED) return fail(ctx, status, "solve diverged (NaN/Inf)");
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,44 @@
+// Tile shapes of the agent sweep kernels and the dispatch over (R, C).
+#pragma once
+
+#include "sweep.cuh"
+
+namespace agents {
+
+// Forward: 16 x 8 threads, 4 pixels per thread -> 64 x 8 pixel tiles.
+constexpr int kFwdPX = 4, kFwdBX = 16, kFwdBY = 8;
+// Adjoint: twice the live state per interaction, so 2 pixels per thread -> 64 x 4 tiles.
+constexpr int kAdjPX = 2, kAdjBX = 32, kAdjBY = 4;
+// Generic (any R, C) kernels: one pixel per thread.
+constexpr int kGenBX = 32, kGenBY = 4;
+
+constexpr int kMaxTiledR = 8;
+
+inline bool tiled_shape(int R, int C) { return R >= 1 && R <= kMaxTiledR && (C == 1 || C == 3); }
+
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Expands F(R, C) for every tiled (R, C) and returns its value; `fallback` otherwise.
+#define AGENTS_DISPATCH_RC(R_, C_, F, fallback)                           \
+  do {                                                                    \
+    if ((C_) == 3) {                                                      \
+      switch (R_) {                                                       \
+        case 1: return F(1, 3); case 2: return F(2, 3);                   \
+        case 3: return F(3, 3); case 4: return F(4, 3);                   \
+        case 5: return F(5, 3); case 6: return F(6, 3);                   \
+        case 7: return F(7, 3); case 8: return F(8, 3);                   \
+        default: break;                                                   \
+      }                                                                   \
+    } else if ((C_) == 1) {                                               \
+      switch (R_) {                                                       \
+        case 1: return F(1, 1); case 2: return F(2, 1);                   \
+        case 3: return F(3, 1); case 4: return F(4, 1);                   \
+        case 5: return F(5, 1); case 6: return F(6, 1);                   \
+        case 7: return F(7, 1); case 8: return F(8, 1);                   \
+        default: break;                                                   \
+      }                                                                   \
+    }                                                                     \
+    return fallback;                                                      \
+  } while (0)
+
+}  // namespace agents

@@ -1,0 +1,100 @@
+// Agent sweep kernels for any window radius and channel count (up to 64 channels): one
+// thread per pixel, the window clipped to the image by the loop bounds.
+#include "sweep.cuh"
+
+namespace agents {
+
+__global__ void forward_generic_kernel(const float* __restrict__ c, float* __restrict__ out,
+                                       const double* __restrict__ eps_n, SweepGeom g) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y * blockDim.y + threadIdx.y;
+  if (q >= g.W || r >= g.H) return;
+  const int C = g.C, R = g.R;
+  const float ex = (float)eps_n[0], ec = (float)eps_n[1];
+  const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
+  const float* ci = c + ((size_t)r * g.W + q) * C;
+  float acc[kGenericMaxC];
+  for (int ch = 0; ch < C; ++ch) acc[ch] = 0.0f;
+  const int y0 = max(r - R, 0), y1 = min(r + R, g.H - 1);
+  const int x0 = max(q - R, 0), x1 = min(q + R, g.W - 1);
+  for (int y = y0; y <= y1; ++y) {
+    const int dy = y - r;
+    const float sy = ky * (float)(dy * dy);
+    for (int x = x0; x <= x1; ++x) {
+      const int dx = x - q;
+      const float* cj = c + ((size_t)y * g.W + x) * C;
+      float s2 = 0.0f;
+      for (int ch = 0; ch < C; ++ch) {
+        const float d = cj[ch] - ci[ch];
+        s2 = fmaf(d, d, s2);
+      }
+      const float ph = wendland_phi(fmaf(kc, s2, fmaf(kx, (float)(dx * dx), sy)));
+      for (int ch = 0; ch < C; ++ch) acc[ch] = fmaf(ph, cj[ch] - ci[ch], acc[ch]);
+    }
+  }
+  float* o = out + ((size_t)r * g.W + q) * C;
+  for (int ch = 0; ch < C; ++ch) o[ch] = fmaf(g.scale, acc[ch], ci[ch]);
+}
+
+__global__ void adjoint_generic_kernel(const float* __restrict__ c,
+                                       const float* __restrict__ lam, float* __restrict__ out,
+                                       const double* __restrict__ eps_n,
+                                       double* __restrict__ partial, SweepGeom g) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y * blockDim.y + threadIdx.y;
+  float Dx = 0.0f, Dc = 0.0f;
+  if (q < g.W && r < g.H) {
+    const int C = g.C, R = g.R;
+    const float ex = (float)eps_n[0], ec = (float)eps_n[1];
+    const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
+    const size_t k = (size_t)r * g.W + q;
+    const float* ck = c + k * C;
+    const float* lk = lam + k * C;
+    float acc[kGenericMaxC];
+    for (int ch = 0; ch < C; ++ch) acc[ch] = 0.0f;
+    const int y0 = max(r - R, 0), y1 = min(r + R, g.H - 1);
+    const int x0 = max(q - R, 0), x1 = min(q + R, g.W - 1);
+    for (int y = y0; y <= y1; ++y) {
+      const int dy = y - r;
+      for (int x = x0; x <= x1; ++x) {
+        const int dx = x - q;
+        const size_t j = (size_t)y * g.W + x;
+        const float* cj = c + j * C;
+        const float* lj = lam + j * C;
+        float s2 = 0.0f, proj = 0.0f, lkd = 0.0f;
+        for (int ch = 0; ch < C; ++ch) {
+          const float d = cj[ch] - ck[ch];
+          s2 = fmaf(d, d, s2);
+          proj = fmaf(d, lj[ch] - lk[ch], proj);
+          lkd = fmaf(lk[ch], d, lkd);
+        }
+        const float sp = fmaf(kx, (float)(dx * dx), ky * (float)(dy * dy));
+        float ph, dph;
+        wendland_phi_dphi(fmaf(kc, s2, sp), ph, dph);
+        const float coef = (dph * ec) * proj;
+        for (int ch = 0; ch < C; ++ch) {
+          const float d = cj[ch] - ck[ch];
+          acc[ch] = fmaf(coef, d, acc[ch]);
+          acc[ch] = fmaf(ph, lj[ch] - lk[ch], acc[ch]);
+        }
+        const float gk = dph * lkd;
+        const float d2 = fmaf(g.inv_w2, (float)(dx * dx), g.inv_h2 * (float)(dy * dy));
+        Dx = fmaf(gk, d2, Dx);
+        Dc = fmaf(gk, s2, Dc);
+      }
+    }
+    float* o = out + k * C;
+    for (int ch = 0; ch < C; ++ch) o[ch] = fmaf(g.scale, acc[ch], lk[ch]);
+  }
+  __shared__ double red[2 * 32];
+  double v[2] = {(double)Dx, (double)Dc};
+  double tot[2];
+  block_sum<2>(v, red, tot);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    partial[2 * b + 0] = tot[0];
+    partial[2 * b + 1] = tot[1];
+  }
+}
+
+}  // namespace agents

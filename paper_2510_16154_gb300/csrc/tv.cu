@@ -1,0 +1,357 @@
+// Total-variation kernels of the ADMM splitting (Section 4.1): the terminal adjoint and
+// objective L~ (Eq. complete_square, Eq. admm_terminal), the shrinkage v-step
+// (Eq. soft_threshold), the multiplier update with its residuals (Eq. dual_ascent), the
+// control projection of Algorithm 1, and deterministic float64 reductions.
+//
+// All are HBM-bound point/stencil kernels.  G is the central-difference gradient with
+// reflective boundaries (Definition discrete_gradient, Eq. reflective_boundary): along
+// x it is (c[q+1] - c[q-1]) / (2 dx) for 1 <= q <= W-2 and exactly 0 on the first and
+// last column (the mirrored neighbour equals the other one); likewise along y.  Its
+// exact transpose is therefore (G_x^T w)[q] = (w[q-1] [q-1 interior] - w[q+1]
+// [q+1 interior]) / (2 dx).  Each thread handles kPPT pixels of one row (strided by the
+// block width, so warps stay coalesced), sums its per-pixel terms in float32 and the
+// block then reduces in float64 with a fixed shuffle tree, writing one partial per block;
+// launch_reduce_rows adds the partials in a fixed order (bitwise reproducible).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace agents {
+
+constexpr int kTvBX = 32, kTvBY = 8, kPPT = 4;
+constexpr int kTvMaxC = 64;
+
+static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+int tv_num_blocks(const TvGeom& g) {
+  return cdiv(g.W, kTvBX * kPPT) * cdiv(g.H, kTvBY);
+}
+
+template <int CT>
+__device__ __forceinline__ int nch(const TvGeom& g) { return CT ? CT : g.C; }
+
+// (G c) at pixel (r, q), channel ch.
+__device__ __forceinline__ float grad_x(const float* __restrict__ c, const TvGeom& g, int r, int q,
+                                        int C, int ch) {
+  if (q < 1 || q > g.W - 2) return 0.0f;
+  const size_t k = (size_t)r * g.W + q;
+  return (__ldg(c + (k + 1) * C + ch) - __ldg(c + (k - 1) * C + ch)) * g.inv2hx;
+}
+__device__ __forceinline__ float grad_y(const float* __restrict__ c, const TvGeom& g, int r, int q,
+                                        int C, int ch) {
+  if (r < 1 || r > g.H - 2) return 0.0f;
+  const size_t k = (size_t)r * g.W + q;
+  return (__ldg(c + (k + g.W) * C + ch) - __ldg(c + (k - g.W) * C + ch)) * g.inv2hy;
+}
+
+// (G c) in float64 (the differences of float32 values are exact in float64).
+__device__ __forceinline__ double grad_x_f64(const float* __restrict__ c, const TvGeom& g, int r,
+                                             int q, int C, int ch) {
+  if (q < 1 || q > g.W - 2) return 0.0;
+  const size_t k = (size_t)r * g.W + q;
+  return ((double)__ldg(c + (k + 1) * C + ch) - (double)__ldg(c + (k - 1) * C + ch)) *
+         (double)g.inv2hx;
+}
+__device__ __forceinline__ double grad_y_f64(const float* __restrict__ c, const TvGeom& g, int r,
+                                             int q, int C, int ch) {
+  if (r < 1 || r > g.H - 2) return 0.0;
+  const size_t k = (size_t)r * g.W + q;
+  return ((double)__ldg(c + (k + g.W) * C + ch) - (double)__ldg(c + (k - g.W) * C + ch)) *
+         (double)g.inv2hy;
+}
+
+// ------------------------------------------------------------------ objective / terminal
+// Per-pixel term of L~ / (dx dy):  rho/2 |v - Gc + mu/rho|^2 + |v| + alpha/2 |c - c0|^2.
+// With LAMBDA, also lam = -dx dy [G^T (rho G c - rho v - mu) + alpha (c - c0)].
+template <int CT, bool LAMBDA>
+__global__ void __launch_bounds__(kTvBX * kTvBY)
+objective_kernel(const float* __restrict__ c, const float* __restrict__ c0,
+                 const float* __restrict__ v, const float* __restrict__ mu,
+                 float* __restrict__ lam, double* __restrict__ partial, TvGeom g) {
+  const int C = nch<CT>(g);
+  const int r = blockIdx.y * kTvBY + threadIdx.y;
+  float acc = 0.0f;
+  if (r < g.H) {
+#pragma unroll
+    for (int i = 0; i < kPPT; ++i) {
+      const int q = blockIdx.x * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
+      if (q >= g.W) break;
+      const size_t k = (size_t)r * g.W + q;
+      const float* vk = v + k * 2 * C;
+      const float* mk = mu + k * 2 * C;
+      float pen = 0.0f, fid = 0.0f, vv = 0.0f, tvs = 0.0f;
+      for (int ch = 0; ch < C; ++ch) {
+        const float gx = grad_x(c, g, r, q, C, ch), gy = grad_y(c, g, r, q, C, ch);
+        const float vx = __ldg(vk + ch), vy = __ldg(vk + C + ch);
+        const float qx = fmaf(__ldg(mk + ch), g.inv_rho, vx - gx);
+        const float qy = fmaf(__ldg(mk + C + ch), g.inv_rho, vy - gy);
+        pen = fmaf(qx, qx, fmaf(qy, qy, pen));
+        const float e = __ldg(c + k * C + ch) - __ldg(c0 + k * C + ch);
+        fid = fmaf(e, e, fid);
+        if (g.tv_mode == 0) vv = fmaf(vx, vx, fmaf(vy, vy, vv));
+        else tvs += sqrtf(fmaf(vx, vx, vy * vy));
+        if constexpr (LAMBDA) {
+          // (G^T w)_k with w = rho G c - rho v - mu, evaluated at the four neighbours
+          float gtw = 0.0f;
+          if (q - 1 >= 1) {  // q - 1 <= W - 2 always holds
+            const size_t m = k - 1;
+            const float w = g.rho * (grad_x(c, g, r, q - 1, C, ch) - __ldg(v + m * 2 * C + ch)) -
+                            __ldg(mu + m * 2 * C + ch);
+            gtw = fmaf(w, g.inv2hx, gtw);
+          }
+          if (q + 1 <= g.W - 2) {
+            const size_t m = k + 1;
+            const float w = g.rho * (grad_x(c, g, r, q + 1, C, ch) - __ldg(v + m * 2 * C + ch)) -
+                            __ldg(mu + m * 2 * C + ch);
+            gtw = fmaf(-w, g.inv2hx, gtw);
+          }
+          if (r - 1 >= 1) {
+            const size_t m = k - g.W;
+            const float w = g.rho * (grad_y(c, g, r - 1, q, C, ch) - __ldg(v + m * 2 * C + C + ch)) -
+                            __ldg(mu + m * 2 * C + C + ch);
+            gtw = fmaf(w, g.inv2hy, gtw);
+          }
+          if (r + 1 <= g.H - 2) {
+            const size_t m = k + g.W;
+            const float w = g.rho * (grad_y(c, g, r + 1, q, C, ch) - __ldg(v + m * 2 * C + C + ch)) -
+                            __ldg(mu + m * 2 * C + C + ch);
+            gtw = fmaf(-w, g.inv2hy, gtw);
+          }
+          lam[k * C + ch] = -(float)g.cell * fmaf(g.alpha, e, gtw);
+        }
+      }
+      const float tv = g.tv_mode == 0 ? sqrtf(vv) : tvs;
+      acc += fmaf(0.5f * g.rho, pen, fmaf(0.5f * g.alpha, fid, tv));
+    }
+  }
+  __shared__ double red[32];
+  double vals[1] = {(double)acc}, tot[1];
+  block_sum<1>(vals, red, tot);
+  if (threadIdx.x == 0 && threadIdx.y == 0)
+    partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = tot[0] * g.cell;
+}
+
+cudaError_t launch_objective(const float* c, const float* c0, const float* v, const float* mu,
+                             float* lam, double* partial, const TvGeom& g, cudaStream_t s) {
+  dim3 grid(cdiv(g.W, kTvBX * kPPT), cdiv(g.H, kTvBY)), block(kTvBX, kTvBY);
+  if (g.C > kTvMaxC) return cudaErrorInvalidValue;
+  if (lam) {
+    if (g.C == 3) objective_kernel<3, true><<<grid, block, 0, s>>>(c, c0, v, mu, lam, partial, g);
+    else if (g.C == 1) objective_kernel<1, true><<<grid, block, 0, s>>>(c, c0, v, mu, lam, partial, g);
+    else objective_kernel<0, true><<<grid, block, 0, s>>>(c, c0, v, mu, lam, partial, g);
+  } else {
+    if (g.C == 3) objective_kernel<3, false><<<grid, block, 0, s>>>(c, c0, v, mu, lam, partial, g);
+    else if (g.C == 1) objective_kernel<1, false><<<grid, block, 0, s>>>(c, c0, v, mu, lam, partial, g);
+    else objective_kernel<0, false><<<grid, block, 0, s>>>(c, c0, v, mu, lam, partial, g);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ v-step (shrinkage)
+// a = G c - mu/rho;  v = a * max(0, 1 - (1/rho)/|a|)  (v = 0 when |a| <= 1/rho).
+template <int CT>
+__global__ void __launch_bounds__(kTvBX * kTvBY)
+pd_tv_kernel(const float* __restrict__ c, const float* __restrict__ mu, float* __restrict__ v,
+             TvGeom g) {
+  const int C = nch<CT>(g);
+  const int r = blockIdx.y * kTvBY + threadIdx.y;
+  if (r >= g.H) return;
+  const float theta = g.inv_rho;
+#pragma unroll
+  for (int i = 0; i < kPPT; ++i) {
+    const int q = blockIdx.x * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
+    if (q >= g.W) break;
+    const size_t k = (size_t)r * g.W + q;
+    const float* mk = mu + k * 2 * C;
+    float* vk = v + k * 2 * C;
+    if (g.tv_mode == 0) {
+      float n2 = 0.0f;
+      for (int ch = 0; ch < C; ++ch) {
+        const float ax = fmaf(-__ldg(mk + ch), g.inv_rho, grad_x(c, g, r, q, C, ch));
+        const float ay = fmaf(-__ldg(mk + C + ch), g.inv_rho, grad_y(c, g, r, q, C, ch));
+        n2 = fmaf(ax, ax, fmaf(ay, ay, n2));
+      }
+      const float n = sqrtf(n2);
+      const float f = n > theta ? 1.0f - theta / n : 0.0f;
+      for (int ch = 0; ch < C; ++ch) {
+        const float ax = fmaf(-__ldg(mk + ch), g.inv_rho, grad_x(c, g, r, q, C, ch));
+        const float ay = fmaf(-__ldg(mk + C + ch), g.inv_rho, grad_y(c, g, r, q, C, ch));
+        vk[ch] = ax * f;
+        vk[C + ch] = ay * f;
+      }
+    } else {
+      for (int ch = 0; ch < C; ++ch) {
+        const float ax = fmaf(-__ldg(mk + ch), g.inv_rho, grad_x(c, g, r, q, C, ch));
+        const float ay = fmaf(-__ldg(mk + C + ch), g.inv_rho, grad_y(c, g, r, q, C, ch));
+        const float n = sqrtf(fmaf(ax, ax, ay * ay));
+        const float f = n > theta ? 1.0f - theta / n : 0.0f;
+        vk[ch] = ax * f;
+        vk[C + ch] = ay * f;
+      }
+    }
+  }
+}
+
+cudaError_t launch_pd_tv_step(const float* c, const float* mu, float* v, const TvGeom& g,
+                              cudaStream_t s) {
+  if (g.C > kTvMaxC) return cudaErrorInvalidValue;
+  dim3 grid(cdiv(g.W, kTvBX * kPPT), cdiv(g.H, kTvBY)), block(kTvBX, kTvBY);
+  if (g.C == 3) pd_tv_kernel<3><<<grid, block, 0, s>>>(c, mu, v, g);
+  else if (g.C == 1) pd_tv_kernel<1><<<grid, block, 0, s>>>(c, mu, v, g);
+  else pd_tv_kernel<0><<<grid, block, 0, s>>>(c, mu, v, g);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ multiplier update
+// mu <- mu + gamma (v - G c), evaluated in float64 (G c included) and rounded once to
+// float32.
+// Per-block partial sums: |v - Gc|^2, |G^T (v - v_prev)|^2, |c - c_prev|^2, |c|^2 and
+// K(c)/(dx dy) = sum |G c_i| + alpha/2 |c_i - c0_i|^2.
+template <int CT>
+__global__ void __launch_bounds__(kTvBX * kTvBY)
+alm_kernel(const float* __restrict__ c, const float* __restrict__ c_prev,
+           const float* __restrict__ c0, const float* __restrict__ v,
+           const float* __restrict__ v_prev, float* __restrict__ mu, double* __restrict__ partial,
+           TvGeom g) {
+  const int C = nch<CT>(g);
+  const int r = blockIdx.y * kTvBY + threadIdx.y;
+  float a_r2 = 0.0f, a_s2 = 0.0f, a_dc2 = 0.0f, a_cn2 = 0.0f, a_K = 0.0f;
+  const double gam = (double)g.gamma;
+  if (r < g.H) {
+#pragma unroll
+    for (int i = 0; i < kPPT; ++i) {
+      const int q = blockIdx.x * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
+      if (q >= g.W) break;
+      const size_t k = (size_t)r * g.W + q;
+      const float* vk = v + k * 2 * C;
+      float* mk = mu + k * 2 * C;
+      float gg2 = 0.0f, tvs = 0.0f, fid = 0.0f;
+      for (int ch = 0; ch < C; ++ch) {
+        const double gxd = grad_x_f64(c, g, r, q, C, ch), gyd = grad_y_f64(c, g, r, q, C, ch);
+        const float vx = __ldg(vk + ch), vy = __ldg(vk + C + ch);
+        const double dxd = (double)vx - gxd, dyd = (double)vy - gyd;
+        mk[ch] = (float)fma(gam, dxd, (double)mk[ch]);
+        mk[C + ch] = (float)fma(gam, dyd, (double)mk[C + ch]);
+        const float gx = (float)gxd, gy = (float)gyd;
+        const float rx = (float)dxd, ry = (float)dyd;
+        a_r2 = fmaf(rx, rx, fmaf(ry, ry, a_r2));
+        if (g.tv_mode == 0) gg2 = fmaf(gx, gx, fmaf(gy, gy, gg2));
+        else tvs += sqrtf(fmaf(gx, gx, gy * gy));
+        const float ck = __ldg(c + k * C + ch);
+        const float e = ck - __ldg(c0 + k * C + ch);
+        fid = fmaf(e, e, fid);
+        a_cn2 = fmaf(ck, ck, a_cn2);
+        if (c_prev) {
+          const float dc = ck - __ldg(c_prev + k * C + ch);
+          a_dc2 = fmaf(dc, dc, a_dc2);
+        }
+        if (v_prev) {
+          // (G^T (v - v_prev))_k
+          float gt = 0.0f;
+          if (q - 1 >= 1) {
+            const size_t m = (k - 1) * 2 * C + ch;
+            gt = fmaf(__ldg(v + m) - __ldg(v_prev + m), g.inv2hx, gt);
+          }
+          if (q + 1 <= g.W - 2) {
+            const size_t m = (k + 1) * 2 * C + ch;
+            gt = fmaf(-(__ldg(v + m) - __ldg(v_prev + m)), g.inv2hx, gt);
+          }
+          if (r - 1 >= 1) {
+            const size_t m = (k - g.W) * 2 * C + C + ch;
+            gt = fmaf(__ldg(v + m) - __ldg(v_prev + m), g.inv2hy, gt);
+          }
+          if (r + 1 <= g.H - 2) {
+            const size_t m = (k + g.W) * 2 * C + C + ch;
+            gt = fmaf(-(__ldg(v + m) - __ldg(v_prev + m)), g.inv2hy, gt);
+          }
+          a_s2 = fmaf(gt, gt, a_s2);
+        }
+      }
+      const float tv = g.tv_mode == 0 ? sqrtf(gg2) : tvs;
+      a_K += fmaf(0.5f * g.alpha, fid, tv);
+    }
+  }
+  __shared__ double red[5 * 32];
+  double vals[5] = {(double)a_r2, (double)a_s2, (double)a_dc2, (double)a_cn2, (double)a_K};
+  double tot[5];
+  block_sum<5>(vals, red, tot);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) partial[5 * b + j] = tot[j];
+  }
+}
+
+cudaError_t launch_alm_update(const float* c, const float* c_prev, const float* c0,
+                              const float* v, const float* v_prev, float* mu, double* partial,
+                              const TvGeom& g, cudaStream_t s) {
+  if (g.C > kTvMaxC) return cudaErrorInvalidValue;
+  dim3 grid(cdiv(g.W, kTvBX * kPPT), cdiv(g.H, kTvBY)), block(kTvBX, kTvBY);
+  if (g.C == 3) alm_kernel<3><<<grid, block, 0, s>>>(c, c_prev, c0, v, v_prev, mu, partial, g);
+  else if (g.C == 1) alm_kernel<1><<<grid, block, 0, s>>>(c, c_prev, c0, v, v_prev, mu, partial, g);
+  else alm_kernel<0><<<grid, block, 0, s>>>(c, c_prev, c0, v, v_prev, mu, partial, g);
+  return cudaGetLastError();
+}
+
+// stats = {sqrt(r2), rho sqrt(s2), gamma dx dy r2, sqrt(dc2 / cn2), dx dy K} from the raw
+// sums {r2, s2, dc2, cn2, K} (one thread).
+__global__ void alm_finalize_kernel(const double* __restrict__ raw, double* __restrict__ st,
+                                    double rho, double gamma, double cell) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  st[0] = sqrt(raw[0]);
+  st[1] = rho * sqrt(raw[1]);
+  st[2] = gamma * cell * raw[0];
+  st[3] = raw[3] > 0.0 ? sqrt(raw[2] / raw[3]) : 0.0;
+  st[4] = cell * raw[4];
+}
+
+cudaError_t launch_alm_finalize(const double* raw, double* stats, double rho, double gamma,
+                                double cell, cudaStream_t s) {
+  alm_finalize_kernel<<<1, 32, 0, s>>>(raw, stats, rho, gamma, cell);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ reductions
+constexpr int kRedThreads = 256;
+
+__global__ void __launch_bounds__(kRedThreads)
+reduce_rows_kernel(const double* __restrict__ partial, int nblocks, int nv, double scale,
+                   double* __restrict__ out) {
+  const int n = blockIdx.x;
+  __shared__ double red[32];
+  for (int k = 0; k < nv; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kRedThreads)
+      s += partial[((size_t)n * nblocks + b) * nv + k];
+    double vals[1] = {s}, tot[1];
+    block_sum<1>(vals, red, tot);
+    if (threadIdx.x == 0) out[(size_t)n * nv + k] = tot[0] * scale;
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_reduce_rows(const double* partial, int nblocks, int nv, int rows,
+                               double scale, double* out, cudaStream_t s) {
+  reduce_rows_kernel<<<rows, kRedThreads, 0, s>>>(partial, nblocks, nv, scale, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ control step
+// trial = Pi_E(eps + tau D): componentwise clip onto the box E (Algorithm 1).
+__global__ void control_step_kernel(const double* __restrict__ eps, const double* __restrict__ D,
+                                    double tau, const double* __restrict__ lo_hi,
+                                    double* __restrict__ trial, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int k = i & 1;
+    const double e = fma(tau, D[i], eps[i]);
+    trial[i] = fmin(fmax(e, lo_hi[k]), lo_hi[2 + k]);
+  }
+}
+
+cudaError_t launch_control_step(const double* eps, const double* D, double tau,
+                                const double* lo_hi, double* trial, int T, cudaStream_t s) {
+  const int n = 2 * T;
+  control_step_kernel<<<cdiv(n, 256), 256, 0, s>>>(eps, D, tau, lo_hi, trial, n);
+  return cudaGetLastError();
+}
+
+}  // namespace agents

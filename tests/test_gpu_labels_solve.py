@@ -1,0 +1,203 @@
+"""GPU parity of the cluster labels (bit-exact: an index computation, decided in float32
+on both sides) and of the full solve (Algorithm 2 with Algorithm 1 inside) against the
+FP64 oracle, plus the error contract of the C ABI on the device path."""
+import os
+
+import numpy as np
+import pytest
+
+from gpuutil import ensure_lib, dev, host, params, f32, zeros_dev, torch
+import oracle
+from oracle.labels import cluster_labels, label_agreement
+from paper_2510_16154_gb300 import lib
+from synth import ImageSpec, make_image, PARITY_64_RGB
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+# ---------------------------------------------------------------- labels
+
+def _snake(H, W):
+    """One component winding through the whole image (worst case for union-find depth)."""
+    c = np.zeros((H, W, 1), dtype=np.float32)
+    for r in range(H):
+        if r % 2 == 1:
+            c[r, :, 0] = 0.9
+            c[r, W - 1 if (r // 2) % 2 == 0 else 0, 0] = 0.0
+    return c
+
+
+@pytest.mark.parametrize("H,W,C,levels", [(1, 1, 3, 4), (1, 37, 3, 4), (37, 1, 1, 3), (50, 70, 3, 6),
+                                          (256, 256, 1, 3), (300, 517, 3, 40)])
+def test_labels_bit_exact(H, W, C, levels):
+    ensure_lib()
+    rng = np.random.default_rng(H + W + C)
+    c = (np.round(rng.uniform(size=(H, W, C)) * levels) / levels * 0.05).astype(np.float32)
+    p, _ = params(H, W, C, 2, 1)
+    with lib.Context(p, dev(c)) as ctx:
+        lab = torch.zeros(H, W, dtype=torch.int32, device="cuda")
+        n = lib.agents_labels(ctx.handle, dev(c), 0.02, lab)
+        got = host(lab)
+    want, count = cluster_labels(c)
+    assert n == count and np.array_equal(got, want)
+
+
+def test_labels_snake_and_threshold_edge():
+    ensure_lib()
+    c = _snake(101, 77)
+    p, _ = params(101, 77, 1, 2, 1)
+    with lib.Context(p, dev(c)) as ctx:
+        lab = np.zeros((101, 77), dtype=np.int32)       # host output
+        n = lib.agents_labels(ctx.handle, dev(c), 0.02, lab)
+    want, count = cluster_labels(c)
+    assert n == count and np.array_equal(lab, want)
+    # exact float32 threshold: a difference of exactly fl32(0.02) joins
+    a = np.float32(0.25)
+    b = np.float32(a + np.float32(0.02))
+    c2 = np.array([[[a], [b], [np.float32(b + np.float32(0.03))]]], dtype=np.float32)
+    p, _ = params(1, 3, 1, 1, 1)
+    with lib.Context(p, dev(c2)) as ctx:
+        lab = np.zeros((1, 3), dtype=np.int32)
+        n = lib.agents_labels(ctx.handle, dev(c2), 0.02, lab)
+    want, count = cluster_labels(c2)
+    assert n == count and np.array_equal(lab, want)
+
+
+# ---------------------------------------------------------------- solve
+
+def _solve_gpu(c0, R, T, k_out, k_in, device_buffers=True, **kw):
+    H, W, C = c0.shape
+    p, op = params(H, W, C, R, T, **kw)
+    o = lib.agents_default_solve_opts()
+    o.k_out, o.k_in = k_out, k_in
+    eps = np.full((T, 2), 57.0)
+    mu = np.zeros((H, W, 2, C), dtype=np.float32)
+    with lib.Context(p, dev(c0, np.float32)) as ctx:
+        if device_buffers:
+            eps_d, mu_d = dev(eps), dev(mu)
+            c_d, v_d = zeros_dev(H, W, C), zeros_dev(H, W, 2, C)
+            lab_d = torch.zeros(H, W, dtype=torch.int32, device="cuda")
+            info = lib.solve(ctx.handle, o, eps_d, mu_d, v_d, c_d, lab_d)
+            out = dict(eps=host(eps_d), mu=host(mu_d), v=host(v_d), c=host(c_d), labels=host(lab_d))
+        else:
+            c_h = np.zeros((H, W, C), dtype=np.float32)
+            v_h = np.zeros((H, W, 2, C), dtype=np.float32)
+            lab_h = np.zeros((H, W), dtype=np.int32)
+            info = lib.solve(ctx.handle, o, eps, mu, v_h, c_h, lab_h)
+            out = dict(eps=eps, mu=mu, v=v_h, c=c_h, labels=lab_h)
+    return out, info, op
+
+
+def test_small_solve_matches_oracle():
+    ensure_lib()
+    c0 = f32(make_image(ImageSpec(20, 24, 3, regions=3, sigma=0.05), 7))
+    out, info, op = _solve_gpu(c0, 2, 4, 3, 3)
+    ref = oracle.admm_solve(c0, op, oracle.SolveOpts(k_out=3, k_in=3))
+    assert info.outer_done == 3
+    assert info.trials == sum(i.trials for i in ref["inner"])
+    assert np.max(np.abs(out["c"] - ref["c"])) <= 1e-4
+    assert np.max(np.abs(out["eps"] - ref["eps"])) <= 1e-3 * np.max(np.abs(ref["eps"]))
+    assert np.max(np.abs(out["mu"] - ref["mu"])) <= 1e-4 * max(1.0, np.max(np.abs(ref["mu"])))
+
+
+def test_host_and_device_buffers_agree():
+    ensure_lib()
+    c0 = f32(make_image(ImageSpec(33, 40, 3, regions=4, sigma=0.05), 3))
+    a, ia, _ = _solve_gpu(c0, 2, 5, 2, 3, device_buffers=True)
+    b, ib, _ = _solve_gpu(c0, 2, 5, 2, 3, device_buffers=False)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    assert ia.as_dict() == ib.as_dict()
+
+
+def test_constant_image_solve_stalls():
+    ensure_lib()
+    c0 = np.full((16, 16, 3), 0.4, dtype=np.float32)
+    out, info, _ = _solve_gpu(c0, 2, 4, 2, 3)
+    assert np.array_equal(out["c"], c0)
+    assert np.all(out["eps"] == 57.0) and info.trials == 0
+    assert info.stationary == 2 and info.stalls == 0   # D = 0: nothing can move
+    assert np.all(out["labels"] == 0)
+
+
+@pytest.mark.parametrize("alpha", [3000.0, 100.0])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_parity_64_rgb_full_solve(seed, alpha):
+    """64x64x3, 4 Voronoi regions, sigma 0.05; R = 2, T = 20, 30 DAL iterations per
+    multiplier step, 10 multiplier steps, against the stored FP64 oracle run (written by
+    tests/golden/make_oracle_parity.py).  Colours within 1e-4 max-abs; cluster labels
+    agree on >= 99.9% of pixels with equal count.
+
+    alpha = 3000 leaves late Armijo tests within float32 rounding of the state (relative
+    differences of L~ near 1e-8), so the two decision traces may part late; those steps
+    move c by ~1e-7.  alpha = 100 has no such near-ties: the traces must be identical."""
+    ensure_lib()
+    path = os.path.join(GOLDEN, f"oracle_parity64_a{int(alpha)}_seed{seed}.npz")
+    if not os.path.exists(path):
+        pytest.fail(f"missing {path}: run tests/golden/make_oracle_parity.py")
+    ref = np.load(path)
+    c0 = f32(make_image(PARITY_64_RGB, seed))
+    H, W, C = c0.shape
+    p, _ = params(H, W, C, 2, 20, alpha=alpha)
+    o = lib.agents_default_solve_opts()
+    o.k_out, o.k_in = 10, 30
+    eps = np.full((20, 2), 57.0)
+    mu = np.zeros((H, W, 2, C), dtype=np.float32)
+    c = np.zeros((H, W, C), dtype=np.float32)
+    labels = np.zeros((H, W), dtype=np.int32)
+    with lib.Context(p, dev(c0, np.float32)) as ctx:
+        info = lib.solve(ctx.handle, o, eps, mu, None, c, labels)
+        log = lib.agents_solve_log(ctx.handle)
+    err = np.max(np.abs(c - ref["c"]))
+    agree = label_agreement(labels, ref["labels"])
+    n_gpu = len(np.unique(labels))
+    trials = np.array([r["trials"] for r in log])
+    print(f"alpha {alpha} seed {seed}: max|dc| {err:.3e} agree {agree:.5f} "
+          f"count {n_gpu}/{int(ref['count'])} trials {trials.sum()}/{int(ref['trials'].sum())}")
+    assert err <= 1e-4
+    assert agree >= 0.999 and n_gpu == int(ref["count"])
+    assert info.outer_done == 10
+    if alpha == 100.0:
+        assert np.array_equal(trials, ref["trials"])
+        assert np.array_equal(np.array([r["tau"] for r in log]), ref["tau"])
+    # the primal-dual gap of the last multiplier step is below that of the first
+    assert info.final_gap < ref["gap"][0]
+
+
+# ---------------------------------------------------------------- error contract
+
+def test_abi_errors_on_device():
+    ensure_lib()
+    c0 = np.full((8, 8, 3), 0.5, dtype=np.float32)
+    p, _ = params(8, 8, 3, 2, 3)
+    with lib.Context(p, dev(c0)) as ctx:
+        v = zeros_dev(8, 8, 2, 3)
+        D = np.zeros((3, 2))
+        eps = np.full((3, 2), 57.0)
+        with pytest.raises(lib.AgentsError) as e:          # adjoint before any stored forward
+            lib.agents_adjoint(ctx.handle, eps, v, v, D)
+        assert e.value.code == lib.AGENTS_ESTATE
+        lib.agents_forward(ctx.handle, eps, None, store=True)
+        with pytest.raises(lib.AgentsError) as e:          # different control
+            lib.agents_adjoint(ctx.handle, eps + 1.0, v, v, D)
+        assert e.value.code == lib.AGENTS_ESTATE
+        lib.agents_adjoint(ctx.handle, eps, v, v, D)       # same control: fine
+        big = torch.zeros(8 * 8 * 3 + 1, device="cuda")
+        with pytest.raises(lib.AgentsError) as e:          # misaligned field pointer
+            lib.pd_tv_step(ctx.handle, big.data_ptr() + 4, v, v)
+        assert e.value.code == lib.AGENTS_EINVAL
+        with pytest.raises(lib.AgentsError) as e:          # NaN control
+            lib.agents_forward(ctx.handle, np.full((3, 2), np.nan), None, store=False)
+        assert e.value.code == lib.AGENTS_EINVAL
+        o = lib.agents_default_solve_opts()
+        o.ls_b = 1.5
+        with pytest.raises(lib.AgentsError) as e:
+            lib.solve(ctx.handle, o, eps.copy(), np.zeros((8, 8, 2, 3), np.float32))
+        assert e.value.code == lib.AGENTS_EINVAL
+    # the context stays usable after errors
+    with lib.Context(p, dev(c0)) as ctx:
+        out = zeros_dev(8, 8, 3)
+        lib.agents_forward(ctx.handle, np.full((3, 2), 57.0), out, store=False)
+        assert np.array_equal(host(out), c0)
