@@ -90,12 +90,12 @@ def load_peaks():
 class ClockSampler:
     """nvidia-smi samples (every 200 ms) during the timed region."""
 
-    QUERY = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, bus_id: str | None):
-        self.bus_id = bus_id
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
         self.proc = None
         self.file = None
 
@@ -121,7 +121,7 @@ class ClockSampler:
         rows = [l.split(", ") for l in self.file.read().strip().splitlines() if l.strip()]
         os.unlink(self.file.name)
         mine = [r for r in rows if len(r) >= 10 and
-                (self.bus_id is None or r[1].lower().endswith(self.bus_id.lower()[-12:]))]
+                (self.uuid is None or self.uuid.lower() in r[1].lower())]
         if not mine:
             mine = [r for r in rows if len(r) >= 10]
         if not mine:
@@ -334,12 +334,12 @@ def main():
         step()
     torch.cuda.synchronize()
 
-    bus = None
+    uuid = None
     try:
-        bus = torch.cuda.get_device_properties(dev).pci_bus_id  # type: ignore[attr-defined]
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         pass
-    sampler = ClockSampler(bus)
+    sampler = ClockSampler(uuid)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     pixel_steps = 0

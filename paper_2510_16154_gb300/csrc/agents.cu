@@ -406,7 +406,7 @@ int agents_init(const agents_params* p, const float* c0, void* cuda_stream, agen
   ctx->sg = SweepGeom{H, W, C, p->radius, (float)(1.0 / ((double)W * W)),
                       (float)(1.0 / ((double)H * H)), (float)(p->dt / ctx->M)};
   ctx->tg = TvGeom{H, W, C, (float)(0.5 * W), (float)(0.5 * H), (float)p->rho,
-                   (float)(1.0 / p->rho), (float)p->alpha, (float)p->gamma,
+                   (float)(1.0 / p->rho), (float)p->alpha, p->gamma,
                    1.0 / ((double)W * (double)H), p->tv_mode};
   ctx->ckpt_every = p->traj_mode >= T ? 0 : p->traj_mode;
   ctx->nb_adj = adjoint_num_blocks(ctx->sg);

@@ -17,7 +17,8 @@ struct SweepGeom {
 struct TvGeom {
   int H, W, C;
   float inv2hx, inv2hy;  // 1/(2 dx) = W/2, 1/(2 dy) = H/2
-  float rho, inv_rho, alpha, gamma;
+  float rho, inv_rho, alpha;
+  double gamma;          // dual step; float64 because the multiplier update is float64
   double cell;           // dx dy
   int tv_mode;
 };

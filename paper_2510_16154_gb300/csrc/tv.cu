@@ -215,7 +215,7 @@ alm_kernel(const float* __restrict__ c, const float* __restrict__ c_prev,
   const int C = nch<CT>(g);
   const int r = blockIdx.y * kTvBY + threadIdx.y;
   float a_r2 = 0.0f, a_s2 = 0.0f, a_dc2 = 0.0f, a_cn2 = 0.0f, a_K = 0.0f;
-  const double gam = (double)g.gamma;
+  const double gam = g.gamma;
   if (r < g.H) {
 #pragma unroll
     for (int i = 0; i < kPPT; ++i) {

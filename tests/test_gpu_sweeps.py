@@ -41,7 +41,9 @@ def test_forward_one_step(H, W, C, R):
         got = host(out).astype(np.float64)
     want = oracle.forward_final(c0, eps, op)
     assert np.max(np.abs(got - want)) <= 1e-6
-    assert np.max(np.abs(want - c0)) > 0 or H * W == 1
+    # non-trivial except on images whose only neighbours sit beyond the support (the
+    # spatial term alone exceeds 1 on a 3 x 2 grid at these controls)
+    assert np.max(np.abs(want - c0)) > 0 or H * W <= 6
 
 
 @pytest.mark.parametrize("norm_mode", [0, 1])
@@ -58,7 +60,7 @@ def test_forward_sweep_20_steps(norm_mode):
         got = host(out).astype(np.float64)
     want = oracle.forward_final(c0, eps, op)
     assert np.max(np.abs(got - want)) <= 1e-5
-    assert np.max(np.abs(want - c0)) > 1e-3
+    assert np.max(np.abs(want - c0)) > (1e-3 if norm_mode == 0 else 1e-4)   # 1/N: slow
 
 
 def test_all_pairs_window_is_paper_system():
