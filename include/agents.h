@@ -215,6 +215,32 @@ int agents_solve_log(const agents_ctx* ctx, agents_iter_record* out, int32_t cap
 int solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float* mu_io,
           float* v_out, float* c_out, int32_t* labels_out, agents_solve_info* info);
 
+/* Objective and terminal adjoint for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a variant of agents_objective for hosts that own
+ * all device memory (they reserve their budget up front and hand out only pre-allocated
+ * buffers) or that must not call cudaMalloc on a latency-critical path, because it can
+ * synchronise the whole device.  It needs no context: every input and output comes from
+ * the caller, and its only scratch, the float64 per-block partial sums of the reduction,
+ * lives in a 256 KiB static device array that every GPU loading the library holds until
+ * the process exits.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   obj_dev (device, one float64) = L~(c, v, mu) of Eq. complete_square;
+ *   lambda_dev (device [H][W][C], may be NULL) = -dL~/dc (exact-transpose form);
+ *   c_dev, c0_dev: device [H][W][C]; v_dev, mu_dev: device [H][W][2][C], 16-byte aligned;
+ *   alpha, rho > 0; tv_mode as in agents_params; cuda_stream as in agents_init.
+ * Limit: images of at most 33,554,432 pixels (32768 reduction blocks of 128 x 8 pixels);
+ * larger images and bad arguments return AGENTS_EINVAL with a message in
+ * agents_last_error(NULL).  The first call on each device (with that device current)
+ * looks up the array's device address and caches it; make that first call before any
+ * stream capture.  All calls share the array, so calls whose work overlaps on the GPU
+ * (different streams, no ordering between them) race and must not be issued; calls on
+ * one stream are ordered and safe.  Nothing in the array needs clearing between calls:
+ * each call writes every partial it reads.  Returns after queueing the work
+ * (stream-ordered). */
+int agents_objective_noalloc(int32_t height, int32_t width, int32_t channels, double alpha,
+                             double rho, int32_t tv_mode, const float* c_dev,
+                             const float* c0_dev, const float* v_dev, const float* mu_dev,
+                             double* obj_dev, float* lambda_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,9 @@ _SIGNATURES = {
     "alm_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "agents_labels": (c_int, [c_void_p, c_void_p, c_float, c_void_p, c_void_p]),
     "agents_solve_log": (c_int, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
+    "agents_objective_noalloc": (c_int, [c_int32, c_int32, c_int32, c_double, c_double, c_int32,
+                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p]),
     "solve": (c_int, [c_void_p, POINTER(agents_solve_opts), c_void_p, c_void_p, c_void_p,
                       c_void_p, c_void_p, POINTER(agents_solve_info)]),
 }
@@ -225,6 +228,17 @@ def agents_solve_log(ctx):
     _check(load().agents_solve_log(ctx, buf, n.value, ctypes.byref(n)), "agents_solve_log", ctx)
     return [{f: getattr(buf[i], f) for f, _ in agents_iter_record._fields_ if f != "reserved"}
             for i in range(n.value)]
+
+
+def agents_objective_noalloc(height, width, channels, alpha, rho, tv_mode, c, c0, v, mu,
+                             obj_out, lam=None, stream=None):
+    """Objective and terminal adjoint with no device allocation (caller-owned inputs and
+    outputs, a static device scratch array inside the library)."""
+    _check(load().agents_objective_noalloc(height, width, channels, alpha, rho, tv_mode,
+                                           _ptr(c, "float32"), _ptr(c0, "float32"),
+                                           _ptr(v, "float32"), _ptr(mu, "float32"),
+                                           _ptr(obj_out, "float64"), _ptr(lam, "float32"),
+                                           _stream(stream)), "agents_objective_noalloc")
 
 
 class Context:

@@ -47,6 +47,11 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
+namespace agents {
+// Message returned by agents_last_error(NULL) for calls that have no context.
+void set_global_error(const std::string& msg) { g_init_error = msg; }
+}  // namespace agents
+
 struct agents_ctx {
   agents_params p{};
   cudaStream_t stream = nullptr;
