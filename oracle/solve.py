@@ -28,7 +28,7 @@ Readings taken here (each also recorded in the design notes):
   sigma are unchanged and the current epsilon-step ends (repeating it would repeat the
   same trials).  sigma carries the accepted tau to the next iteration.
 * Algorithm 2.  mu^(0) = 0 and eps^(0) = 57 (Section 3.2) unless given; the
-  epsilon-argmin of line 5 is approximated by k_in DAL iterations at fixed
+  epsilon-argmin of its control step is approximated by k_in DAL iterations at fixed
   (v^(j-1), mu^(j-1)); gamma = rho (Section 4.2).
 * Stopping.  The "gap" of Section 4.1 is reported as gamma dx dy |v - G c|^2; the
   optional tolerance test is res_j = max(|c^j - c^(j-1)| / |c^j|,
