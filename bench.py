@@ -102,7 +102,9 @@ class ClockSampler:
     def start(self):
         self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}",
+            # bounded: the sampler must not outlive a killed benchmark process
+            self.proc = subprocess.Popen(["timeout", "900", "nvidia-smi",
+                                          f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.file, stderr=subprocess.DEVNULL)
         except OSError:

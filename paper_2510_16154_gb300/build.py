@@ -1,8 +1,10 @@
 """Build ``libagents.so`` (the C-ABI library) in-tree with nvcc for sm_103a.
 
 Every ``csrc/*.cu`` file is compiled in parallel to ``_build/`` at the repository root
-and linked into ``paper_2510_16154_gb300/libagents.so`` with the CUDA runtime linked
-statically, so the library loads without any other CUDA shared object.
+and linked into ``paper_2510_16154_gb300/libagents.so``.  The CUDA runtime is linked
+statically by default, so the library loads without any other CUDA shared object;
+``AGENTS_CUDART=shared`` links ``libcudart.so`` instead (the process then shares one
+runtime instance with other CUDA libraries it loads, e.g. PyTorch's).
 
     python -m paper_2510_16154_gb300.build [--force]
 """
@@ -70,7 +72,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         list(ex.map(compile_one, zip(srcs, objs)))
     tmp = LIB + ".tmp"
-    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    cudart = os.environ.get("AGENTS_CUDART", "static")
+    if cudart not in ("static", "shared"):
+        raise ValueError("AGENTS_CUDART must be 'static' or 'shared'")
+    link = ["-cudart", cudart]
+    if cudart == "shared":
+        cuda_lib = os.path.join(os.path.dirname(os.path.dirname(cc)), "lib64")
+        link += ["-Xlinker", f"-rpath={cuda_lib}"]
+    cmd = [cc, *ARCH, "-shared", *link, "-o", tmp, *objs]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")

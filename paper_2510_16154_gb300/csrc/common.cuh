@@ -26,6 +26,22 @@ __device__ __forceinline__ void wendland_phi_dphi(float r, float& phi, float& dp
   dphi = (-20.0f * rc) * (t2 * t);
 }
 
+// The same functions of s = 1 - r, for callers that form 1 - r directly with one FMA:
+// with t = max(s, 0), phi = t^4 (5 - 4t) and phi' = 20 t^3 (t - 1) (both 0 for r >= 1).
+__device__ __forceinline__ float wendland_phi_1m(float s) {
+  const float t = fmaxf(s, 0.0f);
+  const float t2 = t * t;
+  return (t2 * t2) * fmaf(-4.0f, t, 5.0f);
+}
+
+__device__ __forceinline__ void wendland_phi_dphi_1m(float s, float& phi, float& dphi) {
+  const float t = fmaxf(s, 0.0f);
+  const float t2 = t * t;
+  const float t3 = t2 * t;
+  phi = (t2 * t2) * fmaf(-4.0f, t, 5.0f);
+  dphi = (20.0f * t3) * (t - 1.0f);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int off = kWarp / 2; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);

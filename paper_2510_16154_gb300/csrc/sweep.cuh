@@ -6,11 +6,13 @@
 //  * a CTA owns a TH x TW tile of output pixels; it stages the tile plus an R-pixel halo
 //    of the input field(s) in shared memory, de-interleaved into one plane per channel
 //    (NHWC in HBM -> planar in SMEM), with out-of-image cells zero-filled;
-//  * each thread owns PX consecutive pixels of one row and walks the window row by row:
-//    it loads the PX + 2R cells of that window row once into registers (16- or 8-byte
-//    vector reads) and reuses them for all PX pixels (register blocking);
-//  * the spatial part of r_ij is uniform over pixels, so it is folded into one FMA per
-//    (dy, dx) per thread; phi is branch-free (r clamped at 1);
+//  * each thread owns PXH pixel pairs (one pixel in each half of the tile, same offsets)
+//    and walks the window row by row: it loads that window row's entries once into
+//    registers (16-byte reads) and reuses them for all its pairs (register blocking);
+//  * the arithmetic of a pair runs in packed float2 instructions (sm_100+ FFMA2/FADD2/
+//    FMUL2), halving issued instructions; per lane the operations are the scalar ones;
+//  * the spatial part of r_ij is uniform over pixels, so 1 - r costs one FMA per
+//    interaction from a per-offset constant; phi is branch-free (t = max(1 - r, 0));
 //  * interior tiles skip all bounds handling; tiles whose halo leaves the image multiply
 //    each interaction weight by a 0/1 validity plane (exact: out-of-image cells hold 0,
 //    so the weight times a finite difference is exactly 0);
@@ -23,43 +25,51 @@
 
 namespace agents {
 
-template <int R, int C, int PX, int BX, int BY>
+// Tile geometry.  A CTA owns TH x TW output pixels, TW = 2 HALF.  Thread tx of row ty owns
+// PXH pixel PAIRS: the pixel at tile column tx*PXH + p of the left half and the pixel
+// HALF columns to its right.  Both pixels of a pair see the same window offsets, so all of
+// their arithmetic runs as packed float2 operations (one instruction, two lanes).  Shared
+// memory holds each tile row (with its R-cell halo) as float2 entries
+// e -> (cell e, cell e + HALF), e < HALF + 2R, so the two operands of a pair come from
+// one 8-byte entry and a thread's window row is a run of consecutive entries read with
+// 16-byte loads.
+template <int R, int C, int PXH, int BX, int BY>
 struct Tile {
-  static constexpr int TW = BX * PX;           // tile width (pixels)
-  static constexpr int TH = BY;                // tile height (pixels)
-  static constexpr int NT = BX * BY;           // threads
-  static constexpr int VEC = (PX % 4 == 0) ? 4 : 2;
-  static constexpr int SEG = ((PX + 2 * R + VEC - 1) / VEC) * VEC;  // cells read per row
-  static constexpr int LW = TW + 2 * R;        // loaded width
-  static constexpr int SW0 = (BX - 1) * PX + SEG;
-  static constexpr int SWm = SW0 > LW ? SW0 : LW;
-  static constexpr int SW = ((SWm + 3) / 4) * 4;  // row stride (floats), 16-byte multiple
+  static constexpr int HALF = BX * PXH;          // pixels per half-row
+  static constexpr int TW = 2 * HALF;            // tile width (pixels)
+  static constexpr int TH = BY;                  // tile height (pixels)
+  static constexpr int NT = BX * BY;             // threads
+  static constexpr int NE = HALF + 2 * R;        // paired entries per loaded row
+  static constexpr int SEG = ((PXH + 2 * R + 1) / 2) * 2;   // entries a thread reads per row
+  static constexpr int SW0 = (BX - 1) * PXH + SEG;
+  static constexpr int SWm = SW0 > NE ? SW0 : NE;
+  static constexpr int SW = ((SWm + 1) / 2) * 2; // row stride (entries), 16-byte multiple
   static constexpr int SH = TH + 2 * R;
-  static constexpr int PLANE = SH * SW;
-  static_assert(PX % 2 == 0, "PX must be even");
+  static constexpr int PLANE = SH * SW;          // float2 entries per channel plane
+  static_assert(PXH % 2 == 0, "a thread's first entry must be 16-byte aligned");
 };
 
-template <int VEC, int SEG>
-__device__ __forceinline__ void load_row(const float* __restrict__ row, float (&seg)[SEG]) {
-  if constexpr (VEC == 4) {
+template <int SEG>
+__device__ __forceinline__ void load_row(const float2* __restrict__ row, float2 (&seg)[SEG]) {
 #pragma unroll
-    for (int q = 0; q < SEG / 4; ++q) {
-      const float4 t = reinterpret_cast<const float4*>(row)[q];
-      seg[4 * q + 0] = t.x; seg[4 * q + 1] = t.y; seg[4 * q + 2] = t.z; seg[4 * q + 3] = t.w;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < SEG / 2; ++q) {
-      const float2 t = reinterpret_cast<const float2*>(row)[q];
-      seg[2 * q + 0] = t.x; seg[2 * q + 1] = t.y;
-    }
+  for (int q = 0; q < SEG / 2; ++q) {
+    const float4 t = reinterpret_cast<const float4*>(row)[q];
+    seg[2 * q + 0] = make_float2(t.x, t.y);
+    seg[2 * q + 1] = make_float2(t.z, t.w);
   }
 }
 
-// Stage NF fields (NHWC, C channels each) of the tile + halo into planar shared memory.
-// Returns true when the halo leaves the image (the validity plane is then filled).
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ float2 max0(float2 a) {
+  return make_float2(fmaxf(a.x, 0.0f), fmaxf(a.y, 0.0f));
+}
+
+// Stage NF fields (NHWC, C channels each) of the tile + halo into paired planar shared
+// memory.  Returns true when the halo leaves the image (the validity plane is then
+// filled with 1/0 per cell).
 template <class T, int R, int C, int NF>
-__device__ __forceinline__ bool load_tile(float* __restrict__ sm, float* __restrict__ smask,
+__device__ __forceinline__ bool load_tile(float2* __restrict__ sm, float2* __restrict__ smask,
                                           const float* __restrict__ f0,
                                           const float* __restrict__ f1, const SweepGeom& g,
                                           int x0, int y0) {
@@ -68,96 +78,121 @@ __device__ __forceinline__ bool load_tile(float* __restrict__ sm, float* __restr
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   for (int idx = tid; idx < T::PLANE; idx += T::NT) {
     const int yy = idx / T::SW;
-    const int xx = idx - yy * T::SW;
-    const int gy = y0 - R + yy, gx = x0 - R + xx;
-    const bool ok = xx < T::LW && gy >= 0 && gy < g.H && gx >= 0 && gx < g.W;
-    const size_t base = ok ? ((size_t)gy * g.W + gx) * C : 0;
+    const int k = idx - yy * T::SW;
+    const int gy = y0 - R + yy;
+    const int ga = x0 - R + k, gb = ga + T::HALF;
+    const bool rowok = k < T::NE && gy >= 0 && gy < g.H;
+    const bool oka = rowok && ga >= 0 && ga < g.W;
+    const bool okb = rowok && gb >= 0 && gb < g.W;
+    const size_t ba = oka ? ((size_t)gy * g.W + ga) * C : 0;
+    const size_t bb = okb ? ((size_t)gy * g.W + gb) * C : 0;
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) {
-      sm[ch * T::PLANE + idx] = ok ? __ldg(f0 + base + ch) : 0.0f;
-      if constexpr (NF == 2) sm[(C + ch) * T::PLANE + idx] = ok ? __ldg(f1 + base + ch) : 0.0f;
+      sm[ch * T::PLANE + idx] = make_float2(oka ? __ldg(f0 + ba + ch) : 0.0f,
+                                            okb ? __ldg(f0 + bb + ch) : 0.0f);
+      if constexpr (NF == 2)
+        sm[(C + ch) * T::PLANE + idx] = make_float2(oka ? __ldg(f1 + ba + ch) : 0.0f,
+                                                    okb ? __ldg(f1 + bb + ch) : 0.0f);
     }
-    if (border) smask[idx] = ok ? 1.0f : 0.0f;
+    if (border) smask[idx] = make_float2(oka ? 1.0f : 0.0f, okb ? 1.0f : 0.0f);
   }
   __syncthreads();
   return border;
 }
 
-// ------------------------------------------------------------------ forward step
-template <class T, int R, int C, int PX, bool BORDER>
-__device__ __forceinline__ void forward_body(const float* __restrict__ sm,
-                                             const float* __restrict__ smask,
-                                             float* __restrict__ out, const SweepGeom& g,
-                                             float kx, float ky, float kc, int x0, int y0) {
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int sx = tx * PX;
-  float ci[PX][C], acc[PX][C];
+// Store the pair (left, right) of a thread's p-th pixel pair.
+template <class T, int C, int PXH>
+__device__ __forceinline__ void store_pairs(float* __restrict__ out, const SweepGeom& g,
+                                            const float2 (&base)[PXH][C],
+                                            const float2 (&acc)[PXH][C], int x0, int y0) {
+  const int gy = y0 + threadIdx.y;
+  if (gy >= g.H) return;
 #pragma unroll
-  for (int p = 0; p < PX; ++p)
+  for (int p = 0; p < PXH; ++p) {
+    const int ga = x0 + threadIdx.x * PXH + p, gb = ga + T::HALF;
+    if (ga < g.W) {
+      float* o = out + ((size_t)gy * g.W + ga) * C;
 #pragma unroll
-    for (int ch = 0; ch < C; ++ch) {
-      ci[p][ch] = sm[ch * T::PLANE + (ty + R) * T::SW + sx + R + p];
-      acc[p][ch] = 0.0f;
+      for (int ch = 0; ch < C; ++ch) o[ch] = fmaf(g.scale, acc[p][ch].x, base[p][ch].x);
     }
-#pragma unroll 1
-  for (int dy = -R; dy <= R; ++dy) {
-    const int row = (ty + R + dy) * T::SW + sx;
-    float seg[C][T::SEG];
+    if (gb < g.W) {
+      float* o = out + ((size_t)gy * g.W + gb) * C;
 #pragma unroll
-    for (int ch = 0; ch < C; ++ch) load_row<T::VEC, T::SEG>(sm + ch * T::PLANE + row, seg[ch]);
-    float mseg[BORDER ? T::SEG : 1];
-    if constexpr (BORDER) load_row<T::VEC, T::SEG>(smask + row, mseg);
-    const float sy = ky * (float)(dy * dy);
-#pragma unroll
-    for (int dx = -R; dx <= R; ++dx) {
-      const float sp = fmaf(kx, (float)(dx * dx), sy);
-#pragma unroll
-      for (int p = 0; p < PX; ++p) {
-        const int j = p + R + dx;
-        float d[C];
-        float s2 = 0.0f;
-#pragma unroll
-        for (int ch = 0; ch < C; ++ch) {
-          d[ch] = seg[ch][j] - ci[p][ch];
-          s2 = fmaf(d[ch], d[ch], s2);
-        }
-        float ph = wendland_phi(fmaf(kc, s2, sp));
-        if constexpr (BORDER) ph *= mseg[j];
-#pragma unroll
-        for (int ch = 0; ch < C; ++ch) acc[p][ch] = fmaf(ph, d[ch], acc[p][ch]);
-      }
-    }
-  }
-  const int gy = y0 + ty;
-  if (gy < g.H) {
-#pragma unroll
-    for (int p = 0; p < PX; ++p) {
-      const int gx = x0 + sx + p;
-      if (gx < g.W) {
-        float* o = out + ((size_t)gy * g.W + gx) * C;
-#pragma unroll
-        for (int ch = 0; ch < C; ++ch) o[ch] = fmaf(g.scale, acc[p][ch], ci[p][ch]);
-      }
+      for (int ch = 0; ch < C; ++ch) o[ch] = fmaf(g.scale, acc[p][ch].y, base[p][ch].y);
     }
   }
 }
 
-template <int R, int C, int PX, int BX, int BY>
+// ------------------------------------------------------------------ forward step
+// Per interaction: delta (C), |delta|^2 (C), 1 - r (one FMA: the spatial part of 1 - r is
+// a per-offset constant), phi = t^4 (5 - 4t) with t = max(1 - r, 0), and C updates; every
+// operation is a packed pair except the clamp.
+template <class T, int R, int C, int PXH, bool BORDER>
+__device__ __forceinline__ void forward_body(const float2* __restrict__ sm,
+                                             const float2* __restrict__ smask,
+                                             float* __restrict__ out, const SweepGeom& g,
+                                             float kx, float ky, float kc, int x0, int y0) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int sx = tx * PXH;
+  float2 ci[PXH][C], nci[PXH][C], acc[PXH][C];
+#pragma unroll
+  for (int p = 0; p < PXH; ++p)
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) {
+      ci[p][ch] = sm[ch * T::PLANE + (ty + R) * T::SW + sx + R + p];
+      nci[p][ch] = make_float2(-ci[p][ch].x, -ci[p][ch].y);
+      acc[p][ch] = f2(0.0f);
+    }
+  const float2 nkc = f2(-kc), m4 = f2(-4.0f), five = f2(5.0f);
+#pragma unroll 1
+  for (int dy = -R; dy <= R; ++dy) {
+    const int row = (ty + R + dy) * T::SW + sx;
+    float2 seg[C][T::SEG];
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) load_row<T::SEG>(sm + ch * T::PLANE + row, seg[ch]);
+    float2 mseg[BORDER ? T::SEG : 1];
+    if constexpr (BORDER) load_row<T::SEG>(smask + row, mseg);
+    const float sy = fmaf(-ky, (float)(dy * dy), 1.0f);
+#pragma unroll
+    for (int dx = -R; dx <= R; ++dx) {
+      const float2 sp = f2(fmaf(-kx, (float)(dx * dx), sy));   // 1 - spatial part of r
+#pragma unroll
+      for (int p = 0; p < PXH; ++p) {
+        const int e = p + R + dx;
+        float2 d[C];
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch) d[ch] = __fadd2_rn(seg[ch][e], nci[p][ch]);
+        float2 s2 = __fmul2_rn(d[0], d[0]);
+#pragma unroll
+        for (int ch = 1; ch < C; ++ch) s2 = __ffma2_rn(d[ch], d[ch], s2);
+        const float2 t = max0(__ffma2_rn(nkc, s2, sp));          // max(1 - r, 0)
+        const float2 t2 = __fmul2_rn(t, t);
+        float2 ph = __fmul2_rn(__fmul2_rn(t2, t2), __ffma2_rn(m4, t, five));
+        if constexpr (BORDER) ph = __fmul2_rn(ph, mseg[e]);
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch) acc[p][ch] = __ffma2_rn(ph, d[ch], acc[p][ch]);
+      }
+    }
+  }
+  store_pairs<T, C, PXH>(out, g, ci, acc, x0, y0);
+}
+
+template <int R, int C, int PXH, int BX, int BY>
 __global__ void __launch_bounds__(BX * BY)
 forward_tile_kernel(const float* __restrict__ c, float* __restrict__ out,
                     const double* __restrict__ eps_n, SweepGeom g) {
-  using T = Tile<R, C, PX, BX, BY>;
-  extern __shared__ __align__(16) float smem[];
-  float* sm = smem;
-  float* smask = smem + C * T::PLANE;
+  using T = Tile<R, C, PXH, BX, BY>;
+  extern __shared__ __align__(16) float2 smem2[];
+  float2* sm = smem2;
+  float2* smask = smem2 + C * T::PLANE;
   const int x0 = blockIdx.x * T::TW, y0 = blockIdx.y * T::TH;
   const float ex = (float)eps_n[0], ec = (float)eps_n[1];
   const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
   const bool border = load_tile<T, R, C, 1>(sm, smask, c, nullptr, g, x0, y0);
   if (border)
-    forward_body<T, R, C, PX, true>(sm, smask, out, g, kx, ky, kc, x0, y0);
+    forward_body<T, R, C, PXH, true>(sm, smask, out, g, kx, ky, kc, x0, y0);
   else
-    forward_body<T, R, C, PX, false>(sm, smask, out, g, kx, ky, kc, x0, y0);
+    forward_body<T, R, C, PXH, false>(sm, smask, out, g, kx, ky, kc, x0, y0);
 }
 
 // ------------------------------------------------------------------ adjoint step
@@ -166,89 +201,91 @@ forward_tile_kernel(const float* __restrict__ c, float* __restrict__ out,
 //   symmetric because r_kj = r_jk, the window is symmetric and M is constant);
 // D_x partial = sum_k sum_j phi'(r_kj) |x_j - x_k|^2 (lam_k . delta),
 // D_c partial = sum_k sum_j phi'(r_kj) |delta|^2     (lam_k . delta)   (times 1/(2M) later).
-template <class T, int R, int C, int PX, bool BORDER>
-__device__ __forceinline__ void adjoint_body(const float* __restrict__ sm,
-                                             const float* __restrict__ smask,
+// phi' = 20 t^3 (t - 1) with t = max(1 - r, 0); the factor 20 is applied once per thread.
+template <class T, int R, int C, int PXH, bool BORDER>
+__device__ __forceinline__ void adjoint_body(const float2* __restrict__ sm,
+                                             const float2* __restrict__ smask,
                                              float* __restrict__ out, double* __restrict__ partial,
                                              const SweepGeom& g, float kx, float ky, float kc,
                                              float ec, int x0, int y0) {
-  const float* sc = sm;
-  const float* sl = sm + C * T::PLANE;
+  const float2* sc = sm;
+  const float2* sl = sm + C * T::PLANE;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int sx = tx * PX;
-  float ck[PX][C], lk[PX][C], acc[PX][C];
+  const int sx = tx * PXH;
+  float2 lk[PXH][C], nck[PXH][C], nlk[PXH][C], acc[PXH][C];
 #pragma unroll
-  for (int p = 0; p < PX; ++p)
+  for (int p = 0; p < PXH; ++p)
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) {
       const int o = ch * T::PLANE + (ty + R) * T::SW + sx + R + p;
-      ck[p][ch] = sc[o];
+      const float2 ck = sc[o];
       lk[p][ch] = sl[o];
-      acc[p][ch] = 0.0f;
+      nck[p][ch] = make_float2(-ck.x, -ck.y);
+      nlk[p][ch] = make_float2(-lk[p][ch].x, -lk[p][ch].y);
+      acc[p][ch] = f2(0.0f);
     }
-  float Dx = 0.0f, Dc = 0.0f;
+  const float2 nkc = f2(-kc), m4 = f2(-4.0f), five = f2(5.0f), m1 = f2(-1.0f);
+  const float2 ec20 = f2(20.0f * ec);
+  float2 Dx = f2(0.0f), Dc = f2(0.0f);
 #pragma unroll 1
   for (int dy = -R; dy <= R; ++dy) {
     const int row = (ty + R + dy) * T::SW + sx;
-    float cseg[C][T::SEG], lseg[C][T::SEG];
+    float2 cseg[C][T::SEG], lseg[C][T::SEG];
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) {
-      load_row<T::VEC, T::SEG>(sc + ch * T::PLANE + row, cseg[ch]);
-      load_row<T::VEC, T::SEG>(sl + ch * T::PLANE + row, lseg[ch]);
+      load_row<T::SEG>(sc + ch * T::PLANE + row, cseg[ch]);
+      load_row<T::SEG>(sl + ch * T::PLANE + row, lseg[ch]);
     }
-    float mseg[BORDER ? T::SEG : 1];
-    if constexpr (BORDER) load_row<T::VEC, T::SEG>(smask + row, mseg);
-    const float sy = ky * (float)(dy * dy);
+    float2 mseg[BORDER ? T::SEG : 1];
+    if constexpr (BORDER) load_row<T::SEG>(smask + row, mseg);
+    const float sy = fmaf(-ky, (float)(dy * dy), 1.0f);
     const float d2y = g.inv_h2 * (float)(dy * dy);
 #pragma unroll
     for (int dx = -R; dx <= R; ++dx) {
-      const float sp = fmaf(kx, (float)(dx * dx), sy);
-      const float d2 = fmaf(g.inv_w2, (float)(dx * dx), d2y);
+      const float2 sp = f2(fmaf(-kx, (float)(dx * dx), sy));  // 1 - spatial part of r
+      const float2 d2 = f2(fmaf(g.inv_w2, (float)(dx * dx), d2y));
 #pragma unroll
-      for (int p = 0; p < PX; ++p) {
-        const int j = p + R + dx;
-        float d[C], dl[C];
-        float s2 = 0.0f, proj = 0.0f, lkd = 0.0f;
+      for (int p = 0; p < PXH; ++p) {
+        const int e = p + R + dx;
+        float2 d[C], dl[C];
 #pragma unroll
         for (int ch = 0; ch < C; ++ch) {
-          d[ch] = cseg[ch][j] - ck[p][ch];
-          dl[ch] = lseg[ch][j] - lk[p][ch];
-          s2 = fmaf(d[ch], d[ch], s2);
-          proj = fmaf(d[ch], dl[ch], proj);
-          lkd = fmaf(lk[p][ch], d[ch], lkd);
+          d[ch] = __fadd2_rn(cseg[ch][e], nck[p][ch]);
+          dl[ch] = __fadd2_rn(lseg[ch][e], nlk[p][ch]);
         }
-        float ph, dph;
-        wendland_phi_dphi(fmaf(kc, s2, sp), ph, dph);
+        float2 s2 = __fmul2_rn(d[0], d[0]);
+        float2 proj = __fmul2_rn(d[0], dl[0]);
+        float2 lkd = __fmul2_rn(lk[p][0], d[0]);
+#pragma unroll
+        for (int ch = 1; ch < C; ++ch) {
+          s2 = __ffma2_rn(d[ch], d[ch], s2);
+          proj = __ffma2_rn(d[ch], dl[ch], proj);
+          lkd = __ffma2_rn(lk[p][ch], d[ch], lkd);
+        }
+        const float2 t = max0(__ffma2_rn(nkc, s2, sp));        // max(1 - r, 0)
+        const float2 t2 = __fmul2_rn(t, t);
+        const float2 t3 = __fmul2_rn(t2, t);
+        float2 ph = __fmul2_rn(__fmul2_rn(t2, t2), __ffma2_rn(m4, t, five));
+        float2 dph = __fmul2_rn(t3, __fadd2_rn(t, m1));         // phi' / 20
         if constexpr (BORDER) {
-          ph *= mseg[j];
-          dph *= mseg[j];
+          ph = __fmul2_rn(ph, mseg[e]);
+          dph = __fmul2_rn(dph, mseg[e]);
         }
-        const float coef = (dph * ec) * proj;
+        const float2 coef = __fmul2_rn(__fmul2_rn(dph, ec20), proj);
 #pragma unroll
         for (int ch = 0; ch < C; ++ch) {
-          acc[p][ch] = fmaf(coef, d[ch], acc[p][ch]);
-          acc[p][ch] = fmaf(ph, dl[ch], acc[p][ch]);
+          acc[p][ch] = __ffma2_rn(coef, d[ch], acc[p][ch]);
+          acc[p][ch] = __ffma2_rn(ph, dl[ch], acc[p][ch]);
         }
-        const float gk = dph * lkd;
-        Dx = fmaf(gk, d2, Dx);
-        Dc = fmaf(gk, s2, Dc);
+        const float2 gk = __fmul2_rn(dph, lkd);
+        Dx = __ffma2_rn(gk, d2, Dx);
+        Dc = __ffma2_rn(gk, s2, Dc);
       }
     }
   }
-  const int gy = y0 + ty;
-  if (gy < g.H) {
-#pragma unroll
-    for (int p = 0; p < PX; ++p) {
-      const int gx = x0 + sx + p;
-      if (gx < g.W) {
-        float* o = out + ((size_t)gy * g.W + gx) * C;
-#pragma unroll
-        for (int ch = 0; ch < C; ++ch) o[ch] = fmaf(g.scale, acc[p][ch], lk[p][ch]);
-      }
-    }
-  }
+  store_pairs<T, C, PXH>(out, g, lk, acc, x0, y0);
   __shared__ double red[2 * 32];
-  double v[2] = {(double)Dx, (double)Dc};
+  double v[2] = {20.0 * ((double)Dx.x + (double)Dx.y), 20.0 * ((double)Dc.x + (double)Dc.y)};
   double tot[2];
   block_sum<2>(v, red, tot);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -258,23 +295,23 @@ __device__ __forceinline__ void adjoint_body(const float* __restrict__ sm,
   }
 }
 
-template <int R, int C, int PX, int BX, int BY>
+template <int R, int C, int PXH, int BX, int BY>
 __global__ void __launch_bounds__(BX * BY)
 adjoint_tile_kernel(const float* __restrict__ c, const float* __restrict__ lam,
                     float* __restrict__ out, const double* __restrict__ eps_n,
                     double* __restrict__ partial, SweepGeom g) {
-  using T = Tile<R, C, PX, BX, BY>;
-  extern __shared__ __align__(16) float smem[];
-  float* sm = smem;
-  float* smask = smem + 2 * C * T::PLANE;
+  using T = Tile<R, C, PXH, BX, BY>;
+  extern __shared__ __align__(16) float2 smem2[];
+  float2* sm = smem2;
+  float2* smask = smem2 + 2 * C * T::PLANE;
   const int x0 = blockIdx.x * T::TW, y0 = blockIdx.y * T::TH;
   const float ex = (float)eps_n[0], ec = (float)eps_n[1];
   const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
   const bool border = load_tile<T, R, C, 2>(sm, smask, c, lam, g, x0, y0);
   if (border)
-    adjoint_body<T, R, C, PX, true>(sm, smask, out, partial, g, kx, ky, kc, ec, x0, y0);
+    adjoint_body<T, R, C, PXH, true>(sm, smask, out, partial, g, kx, ky, kc, ec, x0, y0);
   else
-    adjoint_body<T, R, C, PX, false>(sm, smask, out, partial, g, kx, ky, kc, ec, x0, y0);
+    adjoint_body<T, R, C, PXH, false>(sm, smask, out, partial, g, kx, ky, kc, ec, x0, y0);
 }
 
 // ------------------------------------------------------------------ any R, any C

@@ -8,7 +8,7 @@ static cudaError_t adjoint_tiled(const float* c_n, const float* lam_next, float*
                                  const double* eps_n, double* partial, const SweepGeom& g,
                                  cudaStream_t s) {
   using T = Tile<R, C, kAdjPX, kAdjBX, kAdjBY>;
-  const size_t smem = (size_t)(2 * C + 1) * T::PLANE * sizeof(float);
+  const size_t smem = (size_t)(2 * C + 1) * T::PLANE * sizeof(float2);
   auto kern = adjoint_tile_kernel<R, C, kAdjPX, kAdjBX, kAdjBY>;
   if (smem > 48 * 1024) {
     static bool attr_set = false;

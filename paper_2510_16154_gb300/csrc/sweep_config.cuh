@@ -5,10 +5,10 @@
 
 namespace agents {
 
-// Forward: 16 x 8 threads, 4 pixels per thread -> 64 x 8 pixel tiles.
-constexpr int kFwdPX = 4, kFwdBX = 16, kFwdBY = 8;
-// Adjoint: twice the live state per interaction, so 2 pixels per thread -> 64 x 4 tiles.
-constexpr int kAdjPX = 2, kAdjBX = 32, kAdjBY = 4;
+// Forward: 16 x 8 threads, 2 pixel pairs per thread -> 64 x 8 pixel tiles.
+constexpr int kFwdPX = 2, kFwdBX = 16, kFwdBY = 8;
+// Adjoint: 16 x 8 threads, 2 pixel pairs per thread -> 64 x 8 pixel tiles.
+constexpr int kAdjPX = 2, kAdjBX = 16, kAdjBY = 8;
 // Generic (any R, C) kernels: one pixel per thread.
 constexpr int kGenBX = 32, kGenBY = 4;
 

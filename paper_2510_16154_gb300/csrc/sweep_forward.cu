@@ -7,7 +7,7 @@ template <int R, int C>
 static cudaError_t forward_tiled(const float* c_in, float* c_out, const double* eps_n,
                                  const SweepGeom& g, cudaStream_t s) {
   using T = Tile<R, C, kFwdPX, kFwdBX, kFwdBY>;
-  const size_t smem = (size_t)(C + 1) * T::PLANE * sizeof(float);
+  const size_t smem = (size_t)(C + 1) * T::PLANE * sizeof(float2);
   auto kern = forward_tile_kernel<R, C, kFwdPX, kFwdBX, kFwdBY>;
   if (smem > 48 * 1024) {
     static bool attr_set = false;
