@@ -207,6 +207,55 @@ def measure_kernels(torch, lib, dev, stream, size: int, reps: int = 5, only: str
     return out
 
 
+def gradient_workload(torch, lib, dev, reps: int = 3):
+    """Differentiation workload: 2048 x 2048 RGB (24 regions, ramp 0.1, noise 0.1), R = 5,
+    T = 200; forward + backward through the autograd function with checkpoints every 14
+    steps and with the whole trajectory stored.  Reports device time per forward+backward,
+    Mpixel-steps/s (Euler steps incl. recomputation + adjoint steps) and the context's
+    device memory."""
+    from paper_2510_16154_gb300.autograd import FlowContext, flow
+    from synth import make_image, GRADIENT_2048_RGB
+    Hg = Wg = 2048
+    Tg = 200
+    img = torch.from_numpy(make_image(GRADIENT_2048_RGB, 0).astype(np.float32)).to(dev)
+    rng = np.random.default_rng(10)
+    eps0 = np.column_stack([rng.uniform(2, 80, Tg), rng.uniform(2, 80, Tg)])
+    w = torch.from_numpy(rng.normal(size=(Hg, Wg, 3)).astype(np.float32)).to(dev)
+    out = {}
+    for k in (14, 0):
+        p = lib.agents_default_params(Hg, Wg, 3, R, Tg)
+        p.traj_mode = k
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        fc = FlowContext(p, img)
+        foot = free0 - torch.cuda.mem_get_info(dev)[0]
+        eps = torch.tensor(eps0, dtype=torch.float64, device=dev, requires_grad=True)
+
+        def run():
+            eps.grad = None
+            cT = flow(fc, eps, img)
+            cT.backward(gradient=w)
+
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        nseg = (Tg + k - 1) // k if k else 0
+        fwd_steps = Tg + ((Tg - nseg) if k else 0)
+        out[f"checkpoint_{k}" if k else "full_store"] = {
+            "ms_fwd_bwd": t * 1e3, "euler_steps": fwd_steps, "adjoint_steps": Tg,
+            "mpix_steps_per_s": Hg * Wg * (fwd_steps + Tg) / t / 1e6,
+            "context_gb": foot / 1e9}
+        fc.close()
+    return {"workload": "gradient: 2048x2048x3 Voronoi(24)+ramp 0.1+noise 0.1, R=5, T=200, "
+                        "autograd forward+backward", **out}
+
+
 # ---------------------------------------------------------------- CPU oracle leg
 
 ORACLE_ROWS = 256
@@ -287,6 +336,8 @@ def main():
                     help="image side for the per-kernel roofline table (0: skip)")
     ap.add_argument("--kernel", default=None,
                     help="only time this kernel at --kernel-size and exit (profiling driver)")
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "gradient"],
+                    help="gradient: the 2048^2, T=200 differentiation workload (own JSON line)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -311,6 +362,11 @@ def main():
         dist.barrier()
     lib.load()
     stream = torch.cuda.Stream(device=dev)
+    if args.workload == "gradient":
+        res = gradient_workload(torch, lib, dev)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return 0
     if args.kernel:
         res = measure_kernels(torch, lib, dev, stream, args.kernel_size, only=args.kernel)
         if rank == 0:

@@ -111,6 +111,17 @@ int agents_forward(agents_ctx* ctx, const double* eps, float* cT_dev, int store)
 int agents_adjoint(agents_ctx* ctx, const double* eps, const float* v_dev, const float* mu_dev,
                    double* D_out, double* obj_out, float* lambda0_dev);
 
+/* Reverse sweep from a caller-given terminal adjoint, for any terminal cost L(c^T):
+ * with lambdaT_dev = -dL/dc^T (device [H][W][C]) it returns D^n with
+ * dL/deps^n = -dt D^n (D_out, host or device [T][2] float64) and lambda^0 = -dL/dc^0
+ * (lambda0_dev, device [H][W][C], may be NULL) -- the exact discrete adjoint of the
+ * forward sweep (Eq. opt_system-b, Section 3.1).  Requires a preceding
+ * agents_forward(store != 0) with the same eps (else AGENTS_ESTATE); works with full
+ * storage or checkpoints (traj_mode).  This is the backward pass of a differentiable
+ * forward sweep. */
+int agents_adjoint_from(agents_ctx* ctx, const double* eps, const float* lambdaT_dev,
+                        double* D_out, float* lambda0_dev);
+
 /* Terminal cost and adjoint only: obj_out (host or device) = L~(c, v, mu) of
  * Eq. complete_square; lambda_dev (device, may be NULL) = -dL~/dc (Eq. admm_terminal,
  * exact-transpose form).  c_dev: device [H][W][C]. */
@@ -195,6 +206,18 @@ typedef struct {
  * number of records available.  out may be NULL to query the count. */
 int agents_solve_log(const agents_ctx* ctx, agents_iter_record* out, int32_t capacity,
                      int32_t* count);
+
+/* Algorithm 1 on its own (Section 3): the direct-adjoint loop with projected two-way
+ * Armijo search on the terminal cost L~(c(T), 0, 0) = dx dy sum_i [rho/2 |G c_i|^2 +
+ * alpha/2 |c_i - c0_i|^2], which is J of Eq. cost_functional when the context was created
+ * with rho = 1.  Runs at most opts->k_in iterations and stops early when the relative
+ * change of the cost in an iteration is below opts->tol (the stationarity criterion of
+ * the Remark on convergence criteria; tol = 0 disables it) or when the control is
+ * stationary or no step is admissible.  opts->k_out is ignored.  eps_io: host or device
+ * [T][2], in/out; c_out: host or device [H][W][C] = c(T; eps*) (may be NULL).
+ * info->final_obj is the cost after the last accepted step. */
+int dal_solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float* c_out,
+              agents_solve_info* info);
 
 /* Algorithm 2 (ADMM) with Algorithm 1 (DAL + projected two-way Armijo) as the eps-step.
  * The Armijo test is L~(Pi_E(eps + tau D)) < L~(eps) and

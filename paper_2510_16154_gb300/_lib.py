@@ -76,6 +76,7 @@ _SIGNATURES = {
     "agents_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "agents_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "agents_objective": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "agents_adjoint_from": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pd_tv_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "alm_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "agents_labels": (c_int, [c_void_p, c_void_p, c_float, c_void_p, c_void_p]),
@@ -85,6 +86,8 @@ _SIGNATURES = {
                                          c_void_p, c_void_p]),
     "solve": (c_int, [c_void_p, POINTER(agents_solve_opts), c_void_p, c_void_p, c_void_p,
                       c_void_p, c_void_p, POINTER(agents_solve_info)]),
+    "dal_solve": (c_int, [c_void_p, POINTER(agents_solve_opts), c_void_p, c_void_p,
+                          POINTER(agents_solve_info)]),
 }
 
 
@@ -186,6 +189,12 @@ def agents_adjoint(ctx, eps, v, mu, D_out, obj_out=None, lambda0=None):
            "agents_adjoint", ctx)
 
 
+def agents_adjoint_from(ctx, eps, lambdaT, D_out, lambda0=None):
+    _check(load().agents_adjoint_from(ctx, _ptr(eps, "float64"), _ptr(lambdaT, "float32"),
+                                      _ptr(D_out, "float64"), _ptr(lambda0, "float32")),
+           "agents_adjoint_from", ctx)
+
+
 def agents_objective(ctx, c, v, mu, obj_out=None, lam=None):
     _check(load().agents_objective(ctx, _ptr(c, "float32"), _ptr(v, "float32"),
                                    _ptr(mu, "float32"), _ptr(obj_out, "float64"),
@@ -217,6 +226,13 @@ def solve(ctx, opts: agents_solve_opts, eps_io, mu_io, v_out=None, c_out=None,
     _check(load().solve(ctx, ctypes.byref(opts), _ptr(eps_io, "float64"), _ptr(mu_io, "float32"),
                         _ptr(v_out, "float32"), _ptr(c_out, "float32"),
                         _ptr(labels_out, "int32"), ctypes.byref(info)), "solve", ctx)
+    return info
+
+
+def dal_solve(ctx, opts: agents_solve_opts, eps_io, c_out=None) -> agents_solve_info:
+    info = agents_solve_info()
+    _check(load().dal_solve(ctx, ctypes.byref(opts), _ptr(eps_io, "float64"),
+                            _ptr(c_out, "float32"), ctypes.byref(info)), "dal_solve", ctx)
     return info
 
 

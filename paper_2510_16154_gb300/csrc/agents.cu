@@ -245,12 +245,10 @@ int fetch_scalar(agents_ctx* ctx, int slot, double* out) {
   return AGENTS_OK;
 }
 
-// Reverse sweep from lambda^T = -dL~/dc(c^T); D^n (times 1/(2M)) into ctx->d_D.
+// Reverse sweep from lambda^T held in ctx->lam[0]; D^n (times 1/(2M)) into ctx->d_D.
 // Returns the final lambda^0 buffer in *lam_out.
-int adjoint_sweep(agents_ctx* ctx, const double* d_eps, const float* v, const float* mu,
-                  int obj_slot, float** lam_out) {
+int adjoint_sweep_from(agents_ctx* ctx, const double* d_eps, float** lam_out) {
   const int T = ctx->T;
-  TRY(objective(ctx, ctx->cT, v, mu, ctx->lam[0], obj_slot));
   int li = 0;
   const size_t pstride = (size_t)ctx->nb_adj * 2;
   auto step = [&](int n, const float* cn) -> int {
@@ -287,6 +285,13 @@ int adjoint_sweep(agents_ctx* ctx, const double* d_eps, const float* v, const fl
   ++ctx->launches;
   *lam_out = ctx->lam[li];
   return AGENTS_OK;
+}
+
+// Reverse sweep from lambda^T = -dL~/dc(c^T) (the terminal cost of Eq. complete_square).
+int adjoint_sweep(agents_ctx* ctx, const double* d_eps, const float* v, const float* mu,
+                  int obj_slot, float** lam_out) {
+  TRY(objective(ctx, ctx->cT, v, mu, ctx->lam[0], obj_slot));
+  return adjoint_sweep_from(ctx, d_eps, lam_out);
 }
 
 int alm(agents_ctx* ctx, const float* c, const float* c_prev, const float* v,
@@ -337,6 +342,126 @@ int read_control(agents_ctx* ctx, const double* eps, std::vector<double>& host) 
   }
   for (double e : host)
     if (!std::isfinite(e)) return fail(ctx, AGENTS_EINVAL, "control contains NaN/Inf");
+  return AGENTS_OK;
+}
+
+// One iteration of Algorithm 1 on L~(c(T; eps), v, mu), the control in ctx->d_eps:
+// forward sweep with store, terminal adjoint and L~, reverse sweep, then the projected
+// two-way Armijo search (stationarity, sufficient decrease with |P D|^2, strict decrease).
+// Sets `ended` when the eps-step ends (stationary control or no admissible step); appends
+// one record to ctx->log.  Returns AGENTS_EDIVERGED on a NaN/Inf objective.
+int dal_iteration(agents_ctx* ctx, const agents_solve_opts& o, const float* v, const float* mu,
+                  int outer, double& sigma, agents_solve_info& inf, std::vector<double>& Dh,
+                  std::vector<double>& eps_h, bool& ended) {
+  const int T = ctx->T;
+  const double dt = ctx->p.dt;
+  const double lo[2] = {ctx->p.eps_lo[0], ctx->p.eps_lo[1]};
+  const double hi[2] = {ctx->p.eps_hi[0], ctx->p.eps_hi[1]};
+  auto count_fwd = [&]() { inf.forward_steps += T; };
+  ended = false;
+  TRY(forward_sweep(ctx, ctx->d_eps, ctx->cT, true));
+  count_fwd();
+  float* lam0 = nullptr;
+  TRY(adjoint_sweep(ctx, ctx->d_eps, v, mu, 0, &lam0));
+  inf.adjoint_steps += T;
+  inf.tv_sweeps += 1;
+  if (ctx->ckpt_every) inf.forward_steps += T - 1 - ctx->nckpt;
+  double L0;
+  TRY(fetch_scalar(ctx, 0, &L0));
+  CK(cudaMemcpyAsync(Dh.data(), ctx->d_D, Dh.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(eps_h.data(), ctx->d_eps, eps_h.size() * sizeof(double),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ++inf.inner_done;
+  agents_iter_record rec{outer, 0, 0, 0, L0, L0, 0.0, 0.0};
+  if (!std::isfinite(L0)) return AGENTS_EDIVERGED;
+  // Components the projection onto E does not block; |P D|^2 over those only.
+  double g2 = 0.0;
+  bool any_free = false;
+  for (size_t i = 0; i < Dh.size(); ++i) {
+    const int k = (int)(i & 1);
+    const double d = Dh[i], e = eps_h[i];
+    if (d != 0.0 && (e < hi[k] || d < 0.0) && (e > lo[k] || d > 0.0)) {
+      any_free = true;
+      g2 += d * d;
+    }
+  }
+  g2 *= dt;
+  rec.gnorm2 = g2;
+  if (!std::isfinite(g2)) return AGENTS_EDIVERGED;
+  if (!any_free) {  // variational inequality holds: the control is stationary
+    ++inf.stationary;
+    rec.status = 2;
+    ctx->log.push_back(rec);
+    ended = true;
+    return AGENTS_OK;
+  }
+  int cur = 0, best = -1;
+  double best_tau = 0.0, best_L = L0;
+  auto trial = [&](double tau, bool& ok) -> int {
+    CK(launch_control_step(ctx->d_eps, ctx->d_D, tau, ctx->d_lohi, ctx->d_trial[cur], T,
+                           ctx->stream));
+    ++ctx->launches;
+    TRY(forward_sweep(ctx, ctx->d_trial[cur], ctx->s_trial_c, false));
+    count_fwd();
+    TRY(objective(ctx, ctx->s_trial_c, v, mu, nullptr, 1));
+    inf.tv_sweeps += 1;
+    ++inf.trials;
+    double L;
+    TRY(fetch_scalar(ctx, 1, &L));
+    if (!std::isfinite(L)) return AGENTS_EDIVERGED;
+    ok = (L < L0) && (L <= L0 - o.ls_c * tau * g2);
+    if (ok) {
+      best = cur;
+      best_tau = tau;
+      best_L = L;
+      cur ^= 1;  // keep the passing trial; write the next one into the other buffer
+    }
+    return AGENTS_OK;
+  };
+  double tau = sigma;
+  bool ok = false;
+  int ntr = 1;
+  int ts = trial(tau, ok);
+  if (ts != AGENTS_OK) return ts;
+  if (ok) {
+    while (ntr < o.max_ls) {
+      tau = tau / o.ls_b;
+      ++ntr;
+      ts = trial(tau, ok);
+      if (ts != AGENTS_OK || !ok) break;
+    }
+  } else {
+    while (ntr < o.max_ls) {
+      tau = tau * o.ls_b;
+      ++ntr;
+      ts = trial(tau, ok);
+      if (ts != AGENTS_OK || ok) break;
+    }
+  }
+  if (ts != AGENTS_OK) return ts;
+  rec.trials = ntr;
+  if (best < 0) {
+    ++inf.stalls;
+    rec.status = 1;
+    ctx->log.push_back(rec);
+    ended = true;
+    return AGENTS_OK;
+  }
+  rec.L = best_L;
+  rec.tau = best_tau;
+  ctx->log.push_back(rec);
+  CK(cudaMemcpyAsync(ctx->d_eps, ctx->d_trial[best], 2 * (size_t)T * sizeof(double),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  sigma = best_tau;
+  return AGENTS_OK;
+}
+
+int validate_opts(agents_ctx* ctx, const agents_solve_opts& o) {
+  if (o.k_out < 0 || o.k_in < 0 || o.max_ls < 1 || !(o.sigma0 > 0) || !(o.ls_b > 0 && o.ls_b < 1) ||
+      !(o.ls_c > 0 && o.ls_c < 1) || !(o.tol >= 0))
+    return fail(ctx, AGENTS_EINVAL, "invalid solve options");
   return AGENTS_OK;
 }
 
@@ -535,6 +660,28 @@ int agents_adjoint(agents_ctx* ctx, const double* eps, const float* v_dev, const
   return AGENTS_OK;
 }
 
+int agents_adjoint_from(agents_ctx* ctx, const double* eps, const float* lambdaT_dev,
+                        double* D_out, float* lambda0_dev) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  if (!eps || !D_out) return fail(ctx, AGENTS_EINVAL, "eps and D_out must not be NULL");
+  TRY(need(ctx, lambdaT_dev, "lambdaT_dev"));
+  TRY(check_aligned(ctx, lambda0_dev, "lambda0_dev"));
+  DeviceGuard dg(ctx->device);
+  std::vector<double> host;
+  TRY(read_control(ctx, eps, host));
+  if (!ctx->stored || host != ctx->stored_eps)
+    return fail(ctx, AGENTS_ESTATE, "agents_adjoint_from needs a preceding "
+                                    "agents_forward(store=1) with the same control");
+  CK(cudaMemcpyAsync(ctx->lam[0], lambdaT_dev, ctx->nc * sizeof(float),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  float* lam0 = nullptr;
+  TRY(adjoint_sweep_from(ctx, ctx->d_eps, &lam0));
+  if (lambda0_dev) CK(cudaMemcpyAsync(lambda0_dev, lam0, ctx->nc * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+  TRY(from_device(ctx, D_out, ctx->d_D, 2 * (size_t)ctx->T * sizeof(double)));
+  return AGENTS_OK;
+}
+
 int agents_objective(agents_ctx* ctx, const float* c_dev, const float* v_dev,
                      const float* mu_dev, double* obj_out, float* lambda_dev) {
   if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
@@ -600,27 +747,69 @@ int agents_labels(agents_ctx* ctx, const float* c_dev, float threshold, int32_t*
   return AGENTS_OK;
 }
 
+int dal_solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float* c_out,
+              agents_solve_info* info) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  if (!opts || !eps_io) return fail(ctx, AGENTS_EINVAL, "opts and eps_io must not be NULL");
+  const agents_solve_opts o = *opts;
+  TRY(validate_opts(ctx, o));
+  DeviceGuard dg(ctx->device);
+  TRY(ensure_solve_buffers(ctx));
+  const int64_t launches0 = ctx->launches;
+  const int T = ctx->T;
+  agents_solve_info inf{};
+  std::vector<double> eps_h;
+  TRY(read_control(ctx, eps_io, eps_h));
+  ctx->log.clear();
+  CK(cudaMemcpyAsync(ctx->d_eps, eps_h.data(), eps_h.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  // v = mu = 0: L~(c, 0, 0) = dx dy sum [rho/2 |G c|^2 + alpha/2 |c - c0|^2]
+  CK(cudaMemsetAsync(ctx->s_v, 0, ctx->nv * sizeof(float), ctx->stream));
+  CK(cudaMemsetAsync(ctx->s_mu, 0, ctx->nv * sizeof(float), ctx->stream));
+  ctx->stored = false;
+  double sigma = o.sigma0;
+  std::vector<double> Dh(2 * (size_t)T);
+  int status = AGENTS_OK;
+  for (int it = 0; it < o.k_in; ++it) {
+    bool ended = false;
+    status = dal_iteration(ctx, o, ctx->s_v, ctx->s_mu, 1, sigma, inf, Dh, eps_h, ended);
+    if (status != AGENTS_OK || ended) break;
+    const agents_iter_record& r = ctx->log.back();
+    inf.final_obj = r.L;
+    inf.final_res = r.L0 != 0.0 ? std::fabs(r.L - r.L0) / std::fabs(r.L0) : 0.0;
+    if (o.tol > 0.0 && inf.final_res < o.tol) break;   // relative cost change below eta
+  }
+  ctx->stored = false;
+  TRY(from_device(ctx, eps_io, ctx->d_eps, 2 * (size_t)T * sizeof(double)));
+  if (c_out) {
+    TRY(forward_sweep(ctx, ctx->d_eps, ctx->s_c, false));
+    inf.forward_steps += T;
+    TRY(from_device(ctx, c_out, ctx->s_c, ctx->nc * sizeof(float)));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  inf.final_sigma = sigma;
+  inf.kernel_launches = ctx->launches - launches0;
+  if (info) *info = inf;
+  if (status == AGENTS_EDIVERGED) return fail(ctx, status, "DAL diverged (NaN/Inf)");
+  return status;
+}
+
 int solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float* mu_io,
           float* v_out, float* c_out, int32_t* labels_out, agents_solve_info* info) {
   if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
   if (!opts || !eps_io || !mu_io) return fail(ctx, AGENTS_EINVAL, "opts, eps_io, mu_io must not be NULL");
   const agents_solve_opts o = *opts;
-  if (o.k_out < 0 || o.k_in < 0 || o.max_ls < 1 || !(o.sigma0 > 0) || !(o.ls_b > 0 && o.ls_b < 1) ||
-      !(o.ls_c > 0 && o.ls_c < 1) || !(o.tol >= 0))
-    return fail(ctx, AGENTS_EINVAL, "invalid solve options");
+  TRY(validate_opts(ctx, o));
   DeviceGuard dg(ctx->device);
   TRY(ensure_solve_buffers(ctx));
   const int64_t launches0 = ctx->launches;
   const int T = ctx->T;
-  const double dt = ctx->p.dt;
   agents_solve_info inf{};
   auto count_fwd = [&]() { inf.forward_steps += T; };
 
   std::vector<double> eps_h;
   TRY(read_control(ctx, eps_io, eps_h));
   ctx->log.clear();
-  const double lo[2] = {ctx->p.eps_lo[0], ctx->p.eps_lo[1]};
-  const double hi[2] = {ctx->p.eps_hi[0], ctx->p.eps_hi[1]};
   CK(cudaMemcpyAsync(ctx->d_eps, eps_h.data(), eps_h.size() * sizeof(double),
                      cudaMemcpyHostToDevice, ctx->stream));
   TRY(to_device(ctx, ctx->s_mu, mu_io, ctx->nv * sizeof(float)));
@@ -643,100 +832,10 @@ int solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float*
   for (int j = 1; j <= o.k_out && status == AGENTS_OK; ++j) {
     // ---- eps-step: k_in iterations of Algorithm 1 on L~(c(T; eps), v, mu)
     for (int it = 0; it < o.k_in; ++it) {
-      TRY(forward_sweep(ctx, ctx->d_eps, ctx->cT, true));
-      count_fwd();
-      float* lam0 = nullptr;
-      TRY(adjoint_sweep(ctx, ctx->d_eps, v, mu, 0, &lam0));
-      inf.adjoint_steps += T;
-      inf.tv_sweeps += 1;
-      if (ctx->ckpt_every) inf.forward_steps += T - 1 - ctx->nckpt;
-      double L0;
-      TRY(fetch_scalar(ctx, 0, &L0));
-      CK(cudaMemcpyAsync(Dh.data(), ctx->d_D, Dh.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                         ctx->stream));
-      CK(cudaMemcpyAsync(eps_h.data(), ctx->d_eps, eps_h.size() * sizeof(double),
-                         cudaMemcpyDeviceToHost, ctx->stream));
-      CK(cudaStreamSynchronize(ctx->stream));
-      ++inf.inner_done;
-      agents_iter_record rec{j, 0, 0, 0, L0, L0, 0.0, 0.0};
-      if (!std::isfinite(L0)) { status = AGENTS_EDIVERGED; break; }
-      // Components the projection onto E does not block; |P D|^2 over those only.
-      double g2 = 0.0;
-      bool any_free = false;
-      for (size_t i = 0; i < Dh.size(); ++i) {
-        const int k = (int)(i & 1);
-        const double d = Dh[i], e = eps_h[i];
-        if (d != 0.0 && (e < hi[k] || d < 0.0) && (e > lo[k] || d > 0.0)) {
-          any_free = true;
-          g2 += d * d;
-        }
-      }
-      g2 *= dt;
-      rec.gnorm2 = g2;
-      if (!std::isfinite(g2)) { status = AGENTS_EDIVERGED; break; }
-      if (!any_free) {  // variational inequality holds: the control is stationary
-        ++inf.stationary;
-        rec.status = 2;
-        ctx->log.push_back(rec);
-        break;
-      }
-      int cur = 0, best = -1;
-      double best_tau = 0.0, best_L = L0;
-      auto trial = [&](double tau, bool& ok) -> int {
-        CK(launch_control_step(ctx->d_eps, ctx->d_D, tau, ctx->d_lohi, ctx->d_trial[cur], T,
-                               ctx->stream));
-        ++ctx->launches;
-        TRY(forward_sweep(ctx, ctx->d_trial[cur], ctx->s_trial_c, false));
-        count_fwd();
-        TRY(objective(ctx, ctx->s_trial_c, v, mu, nullptr, 1));
-        inf.tv_sweeps += 1;
-        ++inf.trials;
-        double L;
-        TRY(fetch_scalar(ctx, 1, &L));
-        if (!std::isfinite(L)) return AGENTS_EDIVERGED;
-        ok = (L < L0) && (L <= L0 - o.ls_c * tau * g2);
-        if (ok) {
-          best = cur;
-          best_tau = tau;
-          best_L = L;
-          cur ^= 1;  // keep the passing trial; write the next one into the other buffer
-        }
-        return AGENTS_OK;
-      };
-      double tau = sigma;
-      bool ok = false;
-      int ntr = 1;
-      int ts = trial(tau, ok);
-      if (ts != AGENTS_OK) { status = ts; break; }
-      if (ok) {
-        while (ntr < o.max_ls) {
-          tau = tau / o.ls_b;
-          ++ntr;
-          ts = trial(tau, ok);
-          if (ts != AGENTS_OK || !ok) break;
-        }
-      } else {
-        while (ntr < o.max_ls) {
-          tau = tau * o.ls_b;
-          ++ntr;
-          ts = trial(tau, ok);
-          if (ts != AGENTS_OK || ok) break;
-        }
-      }
-      if (ts != AGENTS_OK) { status = ts; break; }
-      rec.trials = ntr;
-      if (best < 0) {
-        ++inf.stalls;
-        rec.status = 1;
-        ctx->log.push_back(rec);
-        break;
-      }
-      rec.L = best_L;
-      rec.tau = best_tau;
-      ctx->log.push_back(rec);
-      CK(cudaMemcpyAsync(ctx->d_eps, ctx->d_trial[best], 2 * (size_t)T * sizeof(double),
-                         cudaMemcpyDeviceToDevice, ctx->stream));
-      sigma = best_tau;
+      bool ended = false;
+      const int st = dal_iteration(ctx, o, v, mu, j, sigma, inf, Dh, eps_h, ended);
+      if (st != AGENTS_OK) { status = st; break; }
+      if (ended) break;
     }
     if (status != AGENTS_OK) break;
     // ---- c^(j), v^(j), mu^(j)

@@ -227,3 +227,28 @@ def test_abi_errors_on_device():
         out = zeros_dev(8, 8, 3)
         lib.agents_forward(ctx.handle, np.full((3, 2), 57.0), out, store=False)
         assert np.array_equal(host(out), c0)
+
+
+# ---------------------------------------------------------------- Algorithm 1 with J
+
+@pytest.mark.parametrize("alpha", [50.0, 2000.0])
+def test_dal_solve_with_J_matches_oracle(alpha):
+    """Algorithm 1 as published (quadratic cost J = L~ with rho = 1, v = mu = 0), stopping
+    on the relative cost change eta = 1e-10 or after 8 iterations, against the oracle."""
+    ensure_lib()
+    c0 = f32(make_image(ImageSpec(32, 40, 3, regions=4, sigma=0.05), 12))
+    T = 8
+    p, op = params(32, 40, 3, 2, T, alpha=alpha, rho=1.0, gamma=1.0)
+    o = lib.agents_default_solve_opts()
+    o.k_in, o.tol = 8, 1e-10
+    eps = np.full((T, 2), 57.0)
+    c = np.zeros((32, 40, 3), dtype=np.float32)
+    with lib.Context(p, dev(c0, np.float32)) as ctx:
+        info = lib.dal_solve(ctx.handle, o, eps, c)
+        log = lib.agents_solve_log(ctx.handle)
+    ref = oracle.dal_solve(c0, op, oracle.SolveOpts(), max_iter=8, eta=1e-10)
+    assert np.max(np.abs(c - ref["c"])) <= 1e-4
+    assert info.final_obj == pytest.approx(ref["log"][-1].L, rel=1e-5)
+    Ls = [r["L"] for r in log if r["status"] == 0]
+    assert all(b <= a for a, b in zip(Ls, Ls[1:]))          # J decreases
+    assert oracle.cost_J(c.astype(np.float64), c0, op) == pytest.approx(info.final_obj, rel=1e-5)
