@@ -190,6 +190,23 @@ typedef struct {
 
 void agents_default_solve_opts(agents_solve_opts* o);
 
+/* Algorithm 2 (with Algorithm 1 inside, exactly as solve()) for n images at once, each in
+ * its own context (any mix of sizes, channel counts and window radii; all with the same
+ * nsteps, traj_mode 0, on one device).  Every Euler / adjoint step of all images is one
+ * persistent launch per (radius, channels) class over a job list of (image, tile) pairs;
+ * the Armijo searches run as per-image state machines on the device, so the launch
+ * sequences of a DAL sweep and of an Armijo round are replayed as CUDA graphs
+ * (use_graph != 0) with one host synchronisation per round for the whole batch.  Images
+ * that reach opts->tol stop while the others continue.  autotune != 0 picks the tile shape
+ * of each class by timing (cached per process); with autotune = 0 every image's result is
+ * bitwise that of solve().  eps_io[i], mu_io[i] (host or device) as in solve(); c_out[i]
+ * (host or device, may be NULL, or c_out itself NULL); infos: host array of n records
+ * (may be NULL; kernel_launches is -1, launches being shared by the batch).  Work is
+ * ordered after the first context's stream; the call returns when it is done. */
+int agents_solve_batch(int32_t n, agents_ctx* const* ctxs, const agents_solve_opts* opts,
+                       int32_t autotune, int32_t use_graph, double* const* eps_io,
+                       float* const* mu_io, float* const* c_out, agents_solve_info* infos);
+
 /* One record per DAL iteration of the last solve() on a context. */
 typedef struct {
   int32_t outer;    /* multiplier step j (1-based)                                       */

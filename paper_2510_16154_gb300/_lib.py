@@ -88,6 +88,9 @@ _SIGNATURES = {
                       c_void_p, c_void_p, POINTER(agents_solve_info)]),
     "dal_solve": (c_int, [c_void_p, POINTER(agents_solve_opts), c_void_p, c_void_p,
                           POINTER(agents_solve_info)]),
+    "agents_solve_batch": (c_int, [c_int32, POINTER(c_void_p), POINTER(agents_solve_opts),
+                                   c_int32, c_int32, POINTER(c_void_p), POINTER(c_void_p),
+                                   POINTER(c_void_p), POINTER(agents_solve_info)]),
 }
 
 
@@ -234,6 +237,23 @@ def dal_solve(ctx, opts: agents_solve_opts, eps_io, c_out=None) -> agents_solve_
     _check(load().dal_solve(ctx, ctypes.byref(opts), _ptr(eps_io, "float64"),
                             _ptr(c_out, "float32"), ctypes.byref(info)), "dal_solve", ctx)
     return info
+
+
+def agents_solve_batch(ctxs, opts: agents_solve_opts, eps_list, mu_list, c_out_list=None,
+                       autotune=False, use_graph=True):
+    """Batched solve of len(ctxs) contexts; returns a list of agents_solve_info."""
+    n = len(ctxs)
+    arr = (c_void_p * n)(*[c.value if isinstance(c, c_void_p) else c for c in ctxs])
+    eps = (c_void_p * n)(*[_ptr(e, "float64") for e in eps_list])
+    mus = (c_void_p * n)(*[_ptr(m, "float32") for m in mu_list])
+    outs = None
+    if c_out_list is not None:
+        outs = (c_void_p * n)(*[_ptr(c, "float32") for c in c_out_list])
+    infos = (agents_solve_info * n)()
+    _check(load().agents_solve_batch(n, arr, ctypes.byref(opts), int(bool(autotune)),
+                                     int(bool(use_graph)), eps, mus, outs, infos),
+           "agents_solve_batch", ctxs[0])
+    return list(infos)
 
 
 def agents_solve_log(ctx):

@@ -7,6 +7,7 @@
 // Everything else (Euler steps, adjoint steps, control projection, reductions) runs in
 // the kernels declared in kernels.h, stream-ordered on the context's stream.
 #include "agents.h"
+#include "ctx_internal.h"
 #include "kernels.h"
 
 #include <algorithm>
@@ -52,55 +53,7 @@ namespace agents {
 void set_global_error(const std::string& msg) { g_init_error = msg; }
 }  // namespace agents
 
-struct agents_ctx {
-  agents_params p{};
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  std::string err;
-
-  int N = 0, C = 0, T = 0;
-  size_t nc = 0, nv = 0;  // floats per colour field, per TV field
-  SweepGeom sg{};
-  TvGeom tg{};
-  double M = 1.0;
-
-  // colour fields
-  float* c0 = nullptr;       // input image c^0
-  float* cT = nullptr;       // c^T of the last stored forward
-  float* work[2] = {nullptr, nullptr};
-  float* lam[2] = {nullptr, nullptr};
-  float* traj = nullptr;     // stored states (mode 0: c^1..c^{T-1}; mode k: checkpoints)
-  float* seg = nullptr;      // mode k: recomputed states of one checkpoint segment
-  int ckpt_every = 0;        // 0: full store; k: checkpoint every k steps
-  int nckpt = 0;
-
-  // control and reductions
-  double* d_eps = nullptr;       // [T][2]
-  double* d_trial[2] = {nullptr, nullptr};
-  double* d_D = nullptr;         // [T][2]
-  double* d_lohi = nullptr;      // [4]
-  double* d_part_adj = nullptr;  // [T][nb_adj][2]
-  double* d_part_tv = nullptr;   // [nb_tv][5]
-  double* d_scal = nullptr;      // [16] small device results
-  double* h_scal = nullptr;      // pinned [16]
-  int nb_adj = 0, nb_tv = 0;
-
-  // labels
-  int32_t* d_labels = nullptr;
-  int32_t* d_lstat = nullptr;    // [2] = {count, status}
-
-  // stored-trajectory bookkeeping
-  bool stored = false;
-  std::vector<double> stored_eps;
-
-  // solve workspaces (allocated on first solve)
-  float *s_c = nullptr, *s_cn = nullptr, *s_v = nullptr, *s_vn = nullptr, *s_mu = nullptr;
-  float* s_trial_c = nullptr;
-
-  int64_t launches = 0;           // kernels launched by this context (for accounting)
-  std::vector<agents_iter_record> log;  // per-DAL-iteration records of the last solve()
-  std::vector<void*> allocs;
-};
+// struct agents_ctx is defined in ctx_internal.h
 
 namespace {
 
@@ -466,6 +419,13 @@ int validate_opts(agents_ctx* ctx, const agents_solve_opts& o) {
 }
 
 }  // namespace
+
+namespace agents {
+int ctx_fail(agents_ctx* ctx, int code, const char* msg) { return fail(ctx, code, "%s", msg); }
+int ctx_forward_sweep(agents_ctx* ctx, const double* d_eps, float* dst_T, bool store) {
+  return forward_sweep(ctx, d_eps, dst_T, store);
+}
+}  // namespace agents
 
 // ====================================================================== C ABI
 extern "C" {

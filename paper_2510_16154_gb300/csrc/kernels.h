@@ -23,6 +23,76 @@ struct TvGeom {
   int tv_mode;
 };
 
+// ---- batched sweeps over many images (one launch per step and (R, C) class) ----
+// Per-image buffers of one context in a batch (full trajectory storage).
+struct BatchSweepImg {
+  SweepGeom g;
+  int nsteps;
+  const float* c0;
+  float* traj;        // c^1 .. c^{T-1}
+  float* work0;       // trial sweep ping-pong
+  float* work1;
+  float* cT;          // c^T of the stored sweep
+  float* trial_c;     // c^T of the trial sweep
+  float* lam0;        // adjoint ping-pong (lam0 holds lambda^T at the start)
+  float* lam1;
+  const double* eps;        // control of the stored sweep, [T][2]
+  const double* trial_eps;  // control of the trial sweep, [T][2]
+  double* part_adj;         // D partials, [T][tiles][2]
+  int ntiles;               // tiles of this image for the shape in use
+};
+struct BatchJob {
+  int img, tx, ty;    // image index and tile (or TV block) coordinates
+};
+enum { kSweepStore = 0, kSweepTrial = 1 };
+// Tile shapes the batched sweeps can use: 64x8, 64x4, 32x8 pixels.
+constexpr int kNumShapes = 3;
+int batch_tile_w(int shape);
+int batch_tile_h(int shape);
+bool batch_tiled(int R, int C);
+// Step n of the forward sweep of `kind` for every job whose image is active.
+cudaError_t launch_forward_batch(const BatchSweepImg* imgs, const BatchJob* jobs, int njobs,
+                                 const int* active, int n, int kind, int R, int C, int shape,
+                                 cudaStream_t s);
+// Step n of the adjoint sweep (reads lam[(T-1-n)&1], writes lam[(T-n)&1], partials of D).
+cudaError_t launch_adjoint_batch(const BatchSweepImg* imgs, const BatchJob* jobs, int njobs,
+                                 const int* active, int n, int R, int C, int shape,
+                                 cudaStream_t s);
+
+// Per-image arguments of a batched TV kernel (the roles each kernel reads are set).
+struct BatchTvArgs {
+  TvGeom g;
+  const float* c;
+  const float* c0;
+  const float* v;
+  const float* mu;
+  float* lam;          // objective: -dL~/dc (may be null)
+  float* v_out;        // pd_tv_step output
+  const float* c_prev; // alm_update
+  const float* v_prev;
+  float* mu_io;
+  double* partial;     // this image's per-block partials
+  int tiles_x;         // TV blocks along x
+};
+int tv_block_w();      // pixels per TV block along x (and kTvBY along y)
+int tv_block_h();
+cudaError_t launch_objective_batch(const BatchTvArgs* args, const BatchJob* jobs, int njobs,
+                                   const int* active, int C, bool lambda, cudaStream_t s);
+cudaError_t launch_pd_tv_batch(const BatchTvArgs* args, const BatchJob* jobs, int njobs,
+                               const int* active, int C, cudaStream_t s);
+cudaError_t launch_alm_batch(const BatchTvArgs* args, const BatchJob* jobs, int njobs,
+                             const int* active, int C, cudaStream_t s);
+// out_s[n * nv + k] = scale_s * sum_b partial_s[(n * nblocks_s + b) * nv + k] for each
+// segment s (blockIdx.y) and row n < rows, in the order of launch_reduce_rows.
+struct ReduceSeg {
+  const double* partial;
+  int nblocks;
+  double scale;
+  double* out;
+};
+cudaError_t launch_reduce_segments(const ReduceSeg* segs, int nseg, int nv, int rows,
+                                   cudaStream_t s);
+
 // ---- agent sweeps (sweep_*.cu) ----
 // One explicit Euler step c_out = c_in + dt F(c_in, eps_n); eps_n points at the device
 // pair (eps_x^n, eps_c^n).

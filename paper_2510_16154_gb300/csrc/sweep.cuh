@@ -288,10 +288,9 @@ __device__ __forceinline__ void adjoint_body(const float2* __restrict__ sm,
   double v[2] = {20.0 * ((double)Dx.x + (double)Dx.y), 20.0 * ((double)Dc.x + (double)Dc.y)};
   double tot[2];
   block_sum<2>(v, red, tot);
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-    partial[2 * b + 0] = tot[0];
-    partial[2 * b + 1] = tot[1];
+  if (threadIdx.x == 0 && threadIdx.y == 0) {   // partial points at this tile's pair
+    partial[0] = tot[0];
+    partial[1] = tot[1];
   }
 }
 
@@ -308,10 +307,89 @@ adjoint_tile_kernel(const float* __restrict__ c, const float* __restrict__ lam,
   const float ex = (float)eps_n[0], ec = (float)eps_n[1];
   const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
   const bool border = load_tile<T, R, C, 2>(sm, smask, c, lam, g, x0, y0);
+  double* part = partial + 2 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x);
   if (border)
-    adjoint_body<T, R, C, PXH, true>(sm, smask, out, partial, g, kx, ky, kc, ec, x0, y0);
+    adjoint_body<T, R, C, PXH, true>(sm, smask, out, part, g, kx, ky, kc, ec, x0, y0);
   else
-    adjoint_body<T, R, C, PXH, false>(sm, smask, out, partial, g, kx, ky, kc, ec, x0, y0);
+    adjoint_body<T, R, C, PXH, false>(sm, smask, out, part, g, kx, ky, kc, ec, x0, y0);
+}
+
+// ------------------------------------------------------------------ batched (persistent)
+// One launch processes step n for every (image, tile) job of a batch; the tile bodies are
+// the single-image ones, so every pixel's result is bitwise the same.  The grid is sized
+// to the resident capacity and walks the job list; jobs of inactive images are skipped.
+__device__ __forceinline__ const float* batch_state(const BatchSweepImg& im, int n) {
+  return n == 0 ? im.c0 : im.traj + (size_t)(n - 1) * im.g.H * im.g.W * im.g.C;
+}
+
+template <int R, int C, int PXH, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY)
+forward_batch_kernel(const BatchSweepImg* __restrict__ imgs, const BatchJob* __restrict__ jobs,
+                     int njobs, const int* __restrict__ active, int n, int kind) {
+  using T = Tile<R, C, PXH, BX, BY>;
+  extern __shared__ __align__(16) float2 smem2[];
+  float2* sm = smem2;
+  float2* smask = smem2 + C * T::PLANE;
+  for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const BatchJob job = jobs[j];
+    if (!active[job.img]) continue;
+    const BatchSweepImg& im = imgs[job.img];
+    const SweepGeom g = im.g;
+    const size_t nc = (size_t)g.H * g.W * C;
+    const float* src;
+    float* dst;
+    const double* eps_n;
+    if (kind == kSweepStore) {
+      src = batch_state(im, n);
+      dst = n == im.nsteps - 1 ? im.cT : im.traj + (size_t)n * nc;
+      eps_n = im.eps + 2 * n;
+    } else {
+      src = n == 0 ? im.c0 : ((n - 1) & 1 ? im.work1 : im.work0);
+      dst = n == im.nsteps - 1 ? im.trial_c : (n & 1 ? im.work1 : im.work0);
+      eps_n = im.trial_eps + 2 * n;
+    }
+    const int x0 = job.tx * T::TW, y0 = job.ty * T::TH;
+    const float ex = (float)eps_n[0], ec = (float)eps_n[1];
+    const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
+    const bool border = load_tile<T, R, C, 1>(sm, smask, src, nullptr, g, x0, y0);
+    if (border)
+      forward_body<T, R, C, PXH, true>(sm, smask, dst, g, kx, ky, kc, x0, y0);
+    else
+      forward_body<T, R, C, PXH, false>(sm, smask, dst, g, kx, ky, kc, x0, y0);
+    __syncthreads();  // the next job reuses shared memory
+  }
+}
+
+template <int R, int C, int PXH, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY)
+adjoint_batch_kernel(const BatchSweepImg* __restrict__ imgs, const BatchJob* __restrict__ jobs,
+                     int njobs, const int* __restrict__ active, int n) {
+  using T = Tile<R, C, PXH, BX, BY>;
+  extern __shared__ __align__(16) float2 smem2[];
+  float2* sm = smem2;
+  float2* smask = smem2 + 2 * C * T::PLANE;
+  for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const BatchJob job = jobs[j];
+    if (!active[job.img]) continue;
+    const BatchSweepImg& im = imgs[job.img];
+    const SweepGeom g = im.g;
+    const int li = (im.nsteps - 1 - n) & 1;
+    const float* lin = li ? im.lam1 : im.lam0;
+    float* lout = li ? im.lam0 : im.lam1;
+    const double* eps_n = im.eps + 2 * n;
+    const int x0 = job.tx * T::TW, y0 = job.ty * T::TH;
+    const float ex = (float)eps_n[0], ec = (float)eps_n[1];
+    const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
+    const bool border = load_tile<T, R, C, 2>(sm, smask, batch_state(im, n), lin, g, x0, y0);
+    const int tiles_x = (g.W + T::TW - 1) / T::TW;
+    // this tile's partial pair, in the single-image kernel's order (row-major tiles)
+    double* part = im.part_adj + ((size_t)n * im.ntiles + (size_t)job.ty * tiles_x + job.tx) * 2;
+    if (border)
+      adjoint_body<T, R, C, PXH, true>(sm, smask, lout, part, g, kx, ky, kc, ec, x0, y0);
+    else
+      adjoint_body<T, R, C, PXH, false>(sm, smask, lout, part, g, kx, ky, kc, ec, x0, y0);
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------------ any R, any C
@@ -325,5 +403,11 @@ __global__ void adjoint_generic_kernel(const float* __restrict__ c,
                                        const float* __restrict__ lam, float* __restrict__ out,
                                        const double* __restrict__ eps_n,
                                        double* __restrict__ partial, SweepGeom g);
+__global__ void forward_generic_batch_kernel(const BatchSweepImg* __restrict__ imgs,
+                                             const BatchJob* __restrict__ jobs, int njobs,
+                                             const int* __restrict__ active, int n, int kind);
+__global__ void adjoint_generic_batch_kernel(const BatchSweepImg* __restrict__ imgs,
+                                             const BatchJob* __restrict__ jobs, int njobs,
+                                             const int* __restrict__ active, int n);
 
 }  // namespace agents

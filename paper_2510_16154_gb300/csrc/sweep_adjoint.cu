@@ -33,6 +33,40 @@ static cudaError_t adjoint_generic(const float* c_n, const float* lam_next, floa
   return cudaGetLastError();
 }
 
+template <int R, int C, int PXH, int BX, int BY>
+static cudaError_t adjoint_batch_tiled(const BatchSweepImg* imgs, const BatchJob* jobs, int njobs,
+                                       const int* active, int n, cudaStream_t s) {
+  using T = Tile<R, C, PXH, BX, BY>;
+  const size_t smem = (size_t)(2 * C + 1) * T::PLANE * sizeof(float2);
+  auto kern = adjoint_batch_kernel<R, C, PXH, BX, BY>;
+  static int cached = 0;
+  int grid = 0;
+  cudaError_t e = persistent_grid(kern, BX * BY, smem, &cached, &grid);
+  if (e != cudaSuccess) return e;
+  grid = grid < njobs ? grid : njobs;
+  if (grid <= 0) return cudaSuccess;
+  kern<<<grid, dim3(BX, BY), smem, s>>>(imgs, jobs, njobs, active, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_batch(const BatchSweepImg* imgs, const BatchJob* jobs, int njobs,
+                                 const int* active, int n, int R, int C, int shape,
+                                 cudaStream_t s) {
+  if (!tiled_shape(R, C)) {
+    if (C > kGenericMaxC) return cudaErrorInvalidValue;
+    const int grid = njobs < 4096 ? njobs : 4096;
+    if (grid <= 0) return cudaSuccess;
+    adjoint_generic_batch_kernel<<<grid, dim3(kGenBX, kGenBY), 0, s>>>(imgs, jobs, njobs, active, n);
+    return cudaGetLastError();
+  }
+#define AGENTS_AB(R_, C_, P_, BX_, BY_) \
+  adjoint_batch_tiled<R_, C_, P_, BX_, BY_>(imgs, jobs, njobs, active, n, s)
+#define AGENTS_ADJ_B(R_, C_) AGENTS_BATCH_SHAPES(AGENTS_AB, R_, C_)
+  AGENTS_DISPATCH_RC(R, C, AGENTS_ADJ_B, cudaErrorInvalidValue);
+#undef AGENTS_ADJ_B
+#undef AGENTS_AB
+}
+
 template <int R, int C>
 static int adjoint_blocks_tiled(const SweepGeom& g) {
   using T = Tile<R, C, kAdjPX, kAdjBX, kAdjBY>;

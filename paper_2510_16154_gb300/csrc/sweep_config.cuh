@@ -18,6 +18,31 @@ inline bool tiled_shape(int R, int C) { return R >= 1 && R <= kMaxTiledR && (C =
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// Opt a kernel into more than 48 KB of dynamic shared memory (once) and return the grid
+// of a persistent launch: every resident block on every SM (computed once).
+template <class K>
+inline cudaError_t persistent_grid(K kern, int threads, size_t smem, int* cached, int* grid) {
+  if (*cached == 0) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int dev = 0, nsm = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    *cached = nsm * (per > 0 ? per : 1);
+  }
+  *grid = *cached;
+  return cudaSuccess;
+}
+
+// Batched tile shapes (pixel pairs per thread, threads in x and y).
+#define AGENTS_BATCH_SHAPES(F, R, C)                                   \
+  (shape == 0 ? F(R, C, 2, 16, 8) : shape == 1 ? F(R, C, 2, 16, 4) : F(R, C, 2, 8, 8))
+
 // Expands F(R, C) for every tiled (R, C) and returns its value; `fallback` otherwise.
 #define AGENTS_DISPATCH_RC(R_, C_, F, fallback)                           \
   do {                                                                    \

@@ -30,6 +30,45 @@ static cudaError_t forward_generic(const float* c_in, float* c_out, const double
   return cudaGetLastError();
 }
 
+template <int R, int C, int PXH, int BX, int BY>
+static cudaError_t forward_batch_tiled(const BatchSweepImg* imgs, const BatchJob* jobs, int njobs,
+                                       const int* active, int n, int kind, cudaStream_t s) {
+  using T = Tile<R, C, PXH, BX, BY>;
+  const size_t smem = (size_t)(C + 1) * T::PLANE * sizeof(float2);
+  auto kern = forward_batch_kernel<R, C, PXH, BX, BY>;
+  static int cached = 0;
+  int grid = 0;
+  cudaError_t e = persistent_grid(kern, BX * BY, smem, &cached, &grid);
+  if (e != cudaSuccess) return e;
+  grid = grid < njobs ? grid : njobs;
+  if (grid <= 0) return cudaSuccess;
+  kern<<<grid, dim3(BX, BY), smem, s>>>(imgs, jobs, njobs, active, n, kind);
+  return cudaGetLastError();
+}
+
+int batch_tile_w(int shape) { return shape == 2 ? 32 : 64; }
+int batch_tile_h(int shape) { return shape == 1 ? 4 : 8; }
+bool batch_tiled(int R, int C) { return tiled_shape(R, C); }
+
+cudaError_t launch_forward_batch(const BatchSweepImg* imgs, const BatchJob* jobs, int njobs,
+                                 const int* active, int n, int kind, int R, int C, int shape,
+                                 cudaStream_t s) {
+  if (!tiled_shape(R, C)) {
+    if (C > kGenericMaxC) return cudaErrorInvalidValue;
+    const int grid = njobs < 4096 ? njobs : 4096;
+    if (grid <= 0) return cudaSuccess;
+    forward_generic_batch_kernel<<<grid, dim3(kGenBX, kGenBY), 0, s>>>(imgs, jobs, njobs, active,
+                                                                      n, kind);
+    return cudaGetLastError();
+  }
+#define AGENTS_FB(R_, C_, P_, BX_, BY_) \
+  forward_batch_tiled<R_, C_, P_, BX_, BY_>(imgs, jobs, njobs, active, n, kind, s)
+#define AGENTS_FWD_B(R_, C_) AGENTS_BATCH_SHAPES(AGENTS_FB, R_, C_)
+  AGENTS_DISPATCH_RC(R, C, AGENTS_FWD_B, cudaErrorInvalidValue);
+#undef AGENTS_FWD_B
+#undef AGENTS_FB
+}
+
 cudaError_t launch_forward_step(const float* c_in, float* c_out, const double* eps_n,
                                 const SweepGeom& g, cudaStream_t s) {
 #define AGENTS_FWD(R, C) forward_tiled<R, C>(c_in, c_out, eps_n, g, s)

@@ -4,10 +4,10 @@
 
 namespace agents {
 
-__global__ void forward_generic_kernel(const float* __restrict__ c, float* __restrict__ out,
-                                       const double* __restrict__ eps_n, SweepGeom g) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void forward_generic_pixel(const float* __restrict__ c,
+                                                      float* __restrict__ out,
+                                                      const double* __restrict__ eps_n,
+                                                      const SweepGeom& g, int q, int r) {
   if (q >= g.W || r >= g.H) return;
   const int C = g.C, R = g.R;
   const float ex = (float)eps_n[0], ec = (float)eps_n[1];
@@ -36,13 +36,21 @@ __global__ void forward_generic_kernel(const float* __restrict__ c, float* __res
   for (int ch = 0; ch < C; ++ch) o[ch] = fmaf(g.scale, acc[ch], ci[ch]);
 }
 
-__global__ void adjoint_generic_kernel(const float* __restrict__ c,
-                                       const float* __restrict__ lam, float* __restrict__ out,
-                                       const double* __restrict__ eps_n,
-                                       double* __restrict__ partial, SweepGeom g) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y * blockDim.y + threadIdx.y;
-  float Dx = 0.0f, Dc = 0.0f;
+__global__ void forward_generic_kernel(const float* __restrict__ c, float* __restrict__ out,
+                                       const double* __restrict__ eps_n, SweepGeom g) {
+  forward_generic_pixel(c, out, eps_n, g, blockIdx.x * blockDim.x + threadIdx.x,
+                        blockIdx.y * blockDim.y + threadIdx.y);
+}
+
+// One pixel of the adjoint step; returns its D partial sums in Dx, Dc.
+__device__ __forceinline__ void adjoint_generic_pixel(const float* __restrict__ c,
+                                                      const float* __restrict__ lam,
+                                                      float* __restrict__ out,
+                                                      const double* __restrict__ eps_n,
+                                                      const SweepGeom& g, int q, int r,
+                                                      float& Dx, float& Dc) {
+  Dx = 0.0f;
+  Dc = 0.0f;
   if (q < g.W && r < g.H) {
     const int C = g.C, R = g.R;
     const float ex = (float)eps_n[0], ec = (float)eps_n[1];
@@ -86,6 +94,15 @@ __global__ void adjoint_generic_kernel(const float* __restrict__ c,
     float* o = out + k * C;
     for (int ch = 0; ch < C; ++ch) o[ch] = fmaf(g.scale, acc[ch], lk[ch]);
   }
+}
+
+__global__ void adjoint_generic_kernel(const float* __restrict__ c,
+                                       const float* __restrict__ lam, float* __restrict__ out,
+                                       const double* __restrict__ eps_n,
+                                       double* __restrict__ partial, SweepGeom g) {
+  float Dx, Dc;
+  adjoint_generic_pixel(c, lam, out, eps_n, g, blockIdx.x * blockDim.x + threadIdx.x,
+                        blockIdx.y * blockDim.y + threadIdx.y, Dx, Dc);
   __shared__ double red[2 * 32];
   double v[2] = {(double)Dx, (double)Dc};
   double tot[2];
@@ -94,6 +111,63 @@ __global__ void adjoint_generic_kernel(const float* __restrict__ c,
     const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
     partial[2 * b + 0] = tot[0];
     partial[2 * b + 1] = tot[1];
+  }
+}
+
+// ------------------------------------------------------------------ batched
+__global__ void forward_generic_batch_kernel(const BatchSweepImg* __restrict__ imgs,
+                                             const BatchJob* __restrict__ jobs, int njobs,
+                                             const int* __restrict__ active, int n, int kind) {
+  for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const BatchJob job = jobs[j];
+    if (!active[job.img]) continue;
+    const BatchSweepImg& im = imgs[job.img];
+    const SweepGeom g = im.g;
+    const size_t nc = (size_t)g.H * g.W * g.C;
+    const float* src;
+    float* dst;
+    const double* eps_n;
+    if (kind == kSweepStore) {
+      src = n == 0 ? im.c0 : im.traj + (size_t)(n - 1) * nc;
+      dst = n == im.nsteps - 1 ? im.cT : im.traj + (size_t)n * nc;
+      eps_n = im.eps + 2 * n;
+    } else {
+      src = n == 0 ? im.c0 : ((n - 1) & 1 ? im.work1 : im.work0);
+      dst = n == im.nsteps - 1 ? im.trial_c : (n & 1 ? im.work1 : im.work0);
+      eps_n = im.trial_eps + 2 * n;
+    }
+    forward_generic_pixel(src, dst, eps_n, g, job.tx * blockDim.x + threadIdx.x,
+                          job.ty * blockDim.y + threadIdx.y);
+  }
+}
+
+__global__ void adjoint_generic_batch_kernel(const BatchSweepImg* __restrict__ imgs,
+                                             const BatchJob* __restrict__ jobs, int njobs,
+                                             const int* __restrict__ active, int n) {
+  __shared__ double red[2 * 32];
+  for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const BatchJob job = jobs[j];
+    if (!active[job.img]) continue;
+    const BatchSweepImg& im = imgs[job.img];
+    const SweepGeom g = im.g;
+    const size_t nc = (size_t)g.H * g.W * g.C;
+    const int li = (im.nsteps - 1 - n) & 1;
+    const float* lin = li ? im.lam1 : im.lam0;
+    float* lout = li ? im.lam0 : im.lam1;
+    const float* cn = n == 0 ? im.c0 : im.traj + (size_t)(n - 1) * nc;
+    float Dx, Dc;
+    adjoint_generic_pixel(cn, lin, lout, im.eps + 2 * n, g, job.tx * blockDim.x + threadIdx.x,
+                          job.ty * blockDim.y + threadIdx.y, Dx, Dc);
+    double v[2] = {(double)Dx, (double)Dc};
+    double tot[2];
+    block_sum<2>(v, red, tot);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const int tiles_x = (g.W + blockDim.x - 1) / blockDim.x;
+      double* part = im.part_adj + ((size_t)n * im.ntiles + (size_t)job.ty * tiles_x + job.tx) * 2;
+      part[0] = tot[0];
+      part[1] = tot[1];
+    }
+    __syncthreads();
   }
 }
 

@@ -62,18 +62,20 @@ __device__ __forceinline__ double grad_y_f64(const float* __restrict__ c, const 
 // ------------------------------------------------------------------ objective / terminal
 // Per-pixel term of L~ / (dx dy):  rho/2 |v - Gc + mu/rho|^2 + |v| + alpha/2 |c - c0|^2.
 // With LAMBDA, also lam = -dx dy [G^T (rho G c - rho v - mu) + alpha (c - c0)].
+// The per-thread part of one block (bx, by) of pixels; returns the thread's float32 sum.
 template <int CT, bool LAMBDA>
-__global__ void __launch_bounds__(kTvBX * kTvBY)
-objective_kernel(const float* __restrict__ c, const float* __restrict__ c0,
-                 const float* __restrict__ v, const float* __restrict__ mu,
-                 float* __restrict__ lam, double* __restrict__ partial, TvGeom g) {
+__device__ __forceinline__ float objective_block(int bx, int by, const float* __restrict__ c,
+                                                 const float* __restrict__ c0,
+                                                 const float* __restrict__ v,
+                                                 const float* __restrict__ mu,
+                                                 float* __restrict__ lam, const TvGeom& g) {
   const int C = nch<CT>(g);
-  const int r = blockIdx.y * kTvBY + threadIdx.y;
+  const int r = by * kTvBY + threadIdx.y;
   float acc = 0.0f;
   if (r < g.H) {
 #pragma unroll
     for (int i = 0; i < kPPT; ++i) {
-      const int q = blockIdx.x * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
+      const int q = bx * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
       if (q >= g.W) break;
       const size_t k = (size_t)r * g.W + q;
       const float* vk = v + k * 2 * C;
@@ -123,6 +125,15 @@ objective_kernel(const float* __restrict__ c, const float* __restrict__ c0,
       acc += fmaf(0.5f * g.rho, pen, fmaf(0.5f * g.alpha, fid, tv));
     }
   }
+  return acc;
+}
+
+template <int CT, bool LAMBDA>
+__global__ void __launch_bounds__(kTvBX * kTvBY)
+objective_kernel(const float* __restrict__ c, const float* __restrict__ c0,
+                 const float* __restrict__ v, const float* __restrict__ mu,
+                 float* __restrict__ lam, double* __restrict__ partial, TvGeom g) {
+  const float acc = objective_block<CT, LAMBDA>(blockIdx.x, blockIdx.y, c, c0, v, mu, lam, g);
   __shared__ double red[32];
   double vals[1] = {(double)acc}, tot[1];
   block_sum<1>(vals, red, tot);
@@ -149,16 +160,16 @@ cudaError_t launch_objective(const float* c, const float* c0, const float* v, co
 // ------------------------------------------------------------------ v-step (shrinkage)
 // a = G c - mu/rho;  v = a * max(0, 1 - (1/rho)/|a|)  (v = 0 when |a| <= 1/rho).
 template <int CT>
-__global__ void __launch_bounds__(kTvBX * kTvBY)
-pd_tv_kernel(const float* __restrict__ c, const float* __restrict__ mu, float* __restrict__ v,
-             TvGeom g) {
+__device__ __forceinline__ void pd_tv_block(int bx, int by, const float* __restrict__ c,
+                                            const float* __restrict__ mu,
+                                            float* __restrict__ v, const TvGeom& g) {
   const int C = nch<CT>(g);
-  const int r = blockIdx.y * kTvBY + threadIdx.y;
+  const int r = by * kTvBY + threadIdx.y;
   if (r >= g.H) return;
   const float theta = g.inv_rho;
 #pragma unroll
   for (int i = 0; i < kPPT; ++i) {
-    const int q = blockIdx.x * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
+    const int q = bx * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
     if (q >= g.W) break;
     const size_t k = (size_t)r * g.W + q;
     const float* mk = mu + k * 2 * C;
@@ -191,6 +202,13 @@ pd_tv_kernel(const float* __restrict__ c, const float* __restrict__ mu, float* _
   }
 }
 
+template <int CT>
+__global__ void __launch_bounds__(kTvBX * kTvBY)
+pd_tv_kernel(const float* __restrict__ c, const float* __restrict__ mu, float* __restrict__ v,
+             TvGeom g) {
+  pd_tv_block<CT>(blockIdx.x, blockIdx.y, c, mu, v, g);
+}
+
 cudaError_t launch_pd_tv_step(const float* c, const float* mu, float* v, const TvGeom& g,
                               cudaStream_t s) {
   if (g.C > kTvMaxC) return cudaErrorInvalidValue;
@@ -207,19 +225,21 @@ cudaError_t launch_pd_tv_step(const float* c, const float* mu, float* v, const T
 // Per-block partial sums: |v - Gc|^2, |G^T (v - v_prev)|^2, |c - c_prev|^2, |c|^2 and
 // K(c)/(dx dy) = sum |G c_i| + alpha/2 |c_i - c0_i|^2.
 template <int CT>
-__global__ void __launch_bounds__(kTvBX * kTvBY)
-alm_kernel(const float* __restrict__ c, const float* __restrict__ c_prev,
-           const float* __restrict__ c0, const float* __restrict__ v,
-           const float* __restrict__ v_prev, float* __restrict__ mu, double* __restrict__ partial,
-           TvGeom g) {
+__device__ __forceinline__ void alm_block(int bx, int by, const float* __restrict__ c,
+                                          const float* __restrict__ c_prev,
+                                          const float* __restrict__ c0,
+                                          const float* __restrict__ v,
+                                          const float* __restrict__ v_prev,
+                                          float* __restrict__ mu, const TvGeom& g,
+                                          float (&out)[5]) {
   const int C = nch<CT>(g);
-  const int r = blockIdx.y * kTvBY + threadIdx.y;
+  const int r = by * kTvBY + threadIdx.y;
   float a_r2 = 0.0f, a_s2 = 0.0f, a_dc2 = 0.0f, a_cn2 = 0.0f, a_K = 0.0f;
   const double gam = g.gamma;
   if (r < g.H) {
 #pragma unroll
     for (int i = 0; i < kPPT; ++i) {
-      const int q = blockIdx.x * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
+      const int q = bx * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
       if (q >= g.W) break;
       const size_t k = (size_t)r * g.W + q;
       const float* vk = v + k * 2 * C;
@@ -270,8 +290,19 @@ alm_kernel(const float* __restrict__ c, const float* __restrict__ c_prev,
       a_K += fmaf(0.5f * g.alpha, fid, tv);
     }
   }
+  out[0] = a_r2; out[1] = a_s2; out[2] = a_dc2; out[3] = a_cn2; out[4] = a_K;
+}
+
+template <int CT>
+__global__ void __launch_bounds__(kTvBX * kTvBY)
+alm_kernel(const float* __restrict__ c, const float* __restrict__ c_prev,
+           const float* __restrict__ c0, const float* __restrict__ v,
+           const float* __restrict__ v_prev, float* __restrict__ mu, double* __restrict__ partial,
+           TvGeom g) {
+  float a[5];
+  alm_block<CT>(blockIdx.x, blockIdx.y, c, c_prev, c0, v, v_prev, mu, g, a);
   __shared__ double red[5 * 32];
-  double vals[5] = {(double)a_r2, (double)a_s2, (double)a_dc2, (double)a_cn2, (double)a_K};
+  double vals[5] = {(double)a[0], (double)a[1], (double)a[2], (double)a[3], (double)a[4]};
   double tot[5];
   block_sum<5>(vals, red, tot);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -332,6 +363,131 @@ reduce_rows_kernel(const double* __restrict__ partial, int nblocks, int nv, doub
 cudaError_t launch_reduce_rows(const double* partial, int nblocks, int nv, int rows,
                                double scale, double* out, cudaStream_t s) {
   reduce_rows_kernel<<<rows, kRedThreads, 0, s>>>(partial, nblocks, nv, scale, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ batched
+int tv_block_w() { return kTvBX * kPPT; }
+int tv_block_h() { return kTvBY; }
+
+template <int CT, bool LAMBDA>
+__global__ void __launch_bounds__(kTvBX * kTvBY)
+objective_batch_kernel(const BatchTvArgs* __restrict__ args, const BatchJob* __restrict__ jobs,
+                       int njobs, const int* __restrict__ active) {
+  __shared__ double red[32];
+  for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const BatchJob job = jobs[j];
+    if (!active[job.img]) continue;
+    const BatchTvArgs& a = args[job.img];
+    const float acc = objective_block<CT, LAMBDA>(job.tx, job.ty, a.c, a.c0, a.v, a.mu, a.lam,
+                                                  a.g);
+    double vals[1] = {(double)acc}, tot[1];
+    block_sum<1>(vals, red, tot);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+      a.partial[(size_t)job.ty * a.tiles_x + job.tx] = tot[0] * a.g.cell;
+    __syncthreads();
+  }
+}
+
+template <int CT>
+__global__ void __launch_bounds__(kTvBX * kTvBY)
+pd_tv_batch_kernel(const BatchTvArgs* __restrict__ args, const BatchJob* __restrict__ jobs,
+                   int njobs, const int* __restrict__ active) {
+  for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const BatchJob job = jobs[j];
+    if (!active[job.img]) continue;
+    const BatchTvArgs& a = args[job.img];
+    pd_tv_block<CT>(job.tx, job.ty, a.c, a.mu, a.v_out, a.g);
+  }
+}
+
+template <int CT>
+__global__ void __launch_bounds__(kTvBX * kTvBY)
+alm_batch_kernel(const BatchTvArgs* __restrict__ args, const BatchJob* __restrict__ jobs,
+                 int njobs, const int* __restrict__ active) {
+  __shared__ double red[5 * 32];
+  for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const BatchJob job = jobs[j];
+    if (!active[job.img]) continue;
+    const BatchTvArgs& a = args[job.img];
+    float o[5];
+    alm_block<CT>(job.tx, job.ty, a.c, a.c_prev, a.c0, a.v, a.v_prev, a.mu_io, a.g, o);
+    double vals[5] = {(double)o[0], (double)o[1], (double)o[2], (double)o[3], (double)o[4]};
+    double tot[5];
+    block_sum<5>(vals, red, tot);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const size_t b = (size_t)job.ty * a.tiles_x + job.tx;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) a.partial[5 * b + k] = tot[k];
+    }
+    __syncthreads();
+  }
+}
+
+static int tv_batch_grid(int njobs) { return njobs < 8192 ? njobs : 8192; }
+
+cudaError_t launch_objective_batch(const BatchTvArgs* args, const BatchJob* jobs, int njobs,
+                                   const int* active, int C, bool lambda, cudaStream_t s) {
+  const int grid = tv_batch_grid(njobs);
+  if (grid <= 0) return cudaSuccess;
+  const dim3 block(kTvBX, kTvBY);
+  if (C > kTvMaxC) return cudaErrorInvalidValue;
+  if (lambda) {
+    if (C == 3) objective_batch_kernel<3, true><<<grid, block, 0, s>>>(args, jobs, njobs, active);
+    else if (C == 1) objective_batch_kernel<1, true><<<grid, block, 0, s>>>(args, jobs, njobs, active);
+    else objective_batch_kernel<0, true><<<grid, block, 0, s>>>(args, jobs, njobs, active);
+  } else {
+    if (C == 3) objective_batch_kernel<3, false><<<grid, block, 0, s>>>(args, jobs, njobs, active);
+    else if (C == 1) objective_batch_kernel<1, false><<<grid, block, 0, s>>>(args, jobs, njobs, active);
+    else objective_batch_kernel<0, false><<<grid, block, 0, s>>>(args, jobs, njobs, active);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pd_tv_batch(const BatchTvArgs* args, const BatchJob* jobs, int njobs,
+                               const int* active, int C, cudaStream_t s) {
+  const int grid = tv_batch_grid(njobs);
+  if (grid <= 0) return cudaSuccess;
+  const dim3 block(kTvBX, kTvBY);
+  if (C > kTvMaxC) return cudaErrorInvalidValue;
+  if (C == 3) pd_tv_batch_kernel<3><<<grid, block, 0, s>>>(args, jobs, njobs, active);
+  else if (C == 1) pd_tv_batch_kernel<1><<<grid, block, 0, s>>>(args, jobs, njobs, active);
+  else pd_tv_batch_kernel<0><<<grid, block, 0, s>>>(args, jobs, njobs, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_alm_batch(const BatchTvArgs* args, const BatchJob* jobs, int njobs,
+                             const int* active, int C, cudaStream_t s) {
+  const int grid = tv_batch_grid(njobs);
+  if (grid <= 0) return cudaSuccess;
+  const dim3 block(kTvBX, kTvBY);
+  if (C > kTvMaxC) return cudaErrorInvalidValue;
+  if (C == 3) alm_batch_kernel<3><<<grid, block, 0, s>>>(args, jobs, njobs, active);
+  else if (C == 1) alm_batch_kernel<1><<<grid, block, 0, s>>>(args, jobs, njobs, active);
+  else alm_batch_kernel<0><<<grid, block, 0, s>>>(args, jobs, njobs, active);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+reduce_segments_kernel(const ReduceSeg* __restrict__ segs, int nv) {
+  const int n = blockIdx.x;
+  const ReduceSeg sg = segs[blockIdx.y];
+  __shared__ double red[32];
+  for (int k = 0; k < nv; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < sg.nblocks; b += kRedThreads)
+      s += sg.partial[((size_t)n * sg.nblocks + b) * nv + k];
+    double vals[1] = {s}, tot[1];
+    block_sum<1>(vals, red, tot);
+    if (threadIdx.x == 0) sg.out[(size_t)n * nv + k] = tot[0] * sg.scale;
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_reduce_segments(const ReduceSeg* segs, int nseg, int nv, int rows,
+                                   cudaStream_t s) {
+  if (nseg <= 0 || rows <= 0) return cudaSuccess;
+  reduce_segments_kernel<<<dim3(rows, nseg), kRedThreads, 0, s>>>(segs, nv);
   return cudaGetLastError();
 }
 

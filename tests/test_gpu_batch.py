@@ -1,0 +1,102 @@
+"""GPU checks of the batched solve (uneven sizes, channel counts and window radii).
+
+With the default tile shape every image of a batch must come out bitwise equal to its own
+solve(): the batched kernels run the same per-pixel arithmetic and the device-side Armijo
+state machine takes the same decisions as the host loop.  This holds with and without
+CUDA-graph replay.  Tolerance stopping ends images independently, and the autotuned run
+yields valid, finite iterates.
+"""
+import numpy as np
+import pytest
+
+from gpuutil import ensure_lib, dev, host, params, f32, torch
+from paper_2510_16154_gb300 import lib
+from synth import ImageSpec, make_image
+
+pytestmark = pytest.mark.gpu
+
+CASES = [  # (H, W, C, R, regions, seed)
+    (40, 56, 3, 2, 4, 1), (23, 70, 3, 3, 3, 2), (64, 33, 1, 2, 5, 3), (17, 19, 3, 2, 2, 4),
+    (31, 45, 5, 2, 3, 5), (48, 48, 3, 3, 6, 6),
+]
+T = 6
+
+
+def _image(H, W, C, K, seed):
+    if C == 5:
+        return f32(make_image(ImageSpec(H, W, C, regions=K, sigma=0.05, spectral=True), seed))
+    return f32(make_image(ImageSpec(H, W, C, regions=K, sigma=0.05), seed))
+
+
+def _opts(k_out=3, k_in=4, tol=0.0):
+    o = lib.agents_default_solve_opts()
+    o.k_out, o.k_in, o.tol = k_out, k_in, tol
+    return o
+
+
+def _single(H, W, C, R, img, o, alpha):
+    p, _ = params(H, W, C, R, T, alpha=alpha)
+    eps = np.full((T, 2), 57.0)
+    mu = np.zeros((H, W, 2, C), dtype=np.float32)
+    c = np.zeros((H, W, C), dtype=np.float32)
+    with lib.Context(p, dev(img, np.float32)) as ctx:
+        info = lib.solve(ctx.handle, o, eps, mu, None, c, None)
+    return eps, mu, c, info
+
+
+def _batch(cases, imgs, o, alpha, **kw):
+    ctxs, eps, mus, cs = [], [], [], []
+    try:
+        for (H, W, C, R, K, seed), img in zip(cases, imgs):
+            p, _ = params(H, W, C, R, T, alpha=alpha)
+            ctxs.append(lib.Context(p, dev(img, np.float32)))
+            eps.append(np.full((T, 2), 57.0))
+            mus.append(np.zeros((H, W, 2, C), dtype=np.float32))
+            cs.append(np.zeros((H, W, C), dtype=np.float32))
+        infos = lib.agents_solve_batch([c.handle for c in ctxs], o, eps, mus, cs, **kw)
+    finally:
+        for c in ctxs:
+            c.close()
+    return eps, mus, cs, infos
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("alpha", [3000.0, 100.0])
+def test_batch_is_bitwise_equal_to_single_solves(use_graph, alpha):
+    ensure_lib()
+    imgs = [_image(H, W, C, K, seed) for H, W, C, R, K, seed in CASES]
+    o = _opts()
+    eps_b, mu_b, c_b, infos = _batch(CASES, imgs, o, alpha, autotune=False, use_graph=use_graph)
+    for k, ((H, W, C, R, K, seed), img) in enumerate(zip(CASES, imgs)):
+        eps, mu, c, info = _single(H, W, C, R, img, o, alpha)
+        assert np.array_equal(eps_b[k], eps), k
+        assert np.array_equal(mu_b[k], mu), k
+        assert np.array_equal(c_b[k], c), k
+        assert infos[k].trials == info.trials and infos[k].outer_done == info.outer_done
+        assert infos[k].forward_steps == info.forward_steps
+        assert infos[k].adjoint_steps == info.adjoint_steps
+
+
+def test_batch_tolerance_stops_images_independently():
+    ensure_lib()
+    cases = CASES[:4] + [(20, 20, 3, 2, 1, 9)]          # last: one region, no noise left
+    imgs = [_image(H, W, C, K, seed) for H, W, C, R, K, seed in cases[:4]]
+    imgs.append(np.full((20, 20, 3), 0.4, dtype=np.float32))
+    o = _opts(k_out=6, k_in=3, tol=1e-4)
+    _, _, c_b, infos = _batch(cases, imgs, o, 3000.0, autotune=False, use_graph=True)
+    assert infos[-1].outer_done == 1                      # constant image: res = 0 at once
+    for k, ((H, W, C, R, K, seed), img) in enumerate(zip(cases, imgs)):
+        _, _, c, info = _single(H, W, C, R, img, o, 3000.0)
+        assert infos[k].outer_done == info.outer_done
+        assert np.array_equal(c_b[k], c)
+
+
+def test_batch_autotuned_is_valid():
+    ensure_lib()
+    imgs = [_image(H, W, C, K, seed) for H, W, C, R, K, seed in CASES]
+    o = _opts()
+    eps_b, _, c_b, infos = _batch(CASES, imgs, o, 3000.0, autotune=True, use_graph=True)
+    for k, (H, W, C, R, K, seed) in enumerate(CASES):
+        assert np.all(np.isfinite(c_b[k])) and np.all(np.isfinite(eps_b[k]))
+        assert np.all(eps_b[k] >= 2.0) and np.all(eps_b[k] <= 1100.0)
+        assert infos[k].outer_done == 3
