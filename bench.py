@@ -256,6 +256,101 @@ def gradient_workload(torch, lib, dev, reps: int = 3):
                         "autograd forward+backward", **out}
 
 
+BATCH_T = 20
+BATCH_K_IN = 4
+
+
+def batch_workload(torch, lib, dev, count: int, scale: float, steps: int, warmup: int,
+                   tol_outer: int):
+    """Batching workload: `count` images of uneven size (sides H ~ U{128..1536} times
+    `scale`, aspect U[0.5, 2]), two thirds RGB and one third 31-band spectra, window
+    radius U{3..7} per image, T = 20.  One step = agents_solve_batch(k_out = 1,
+    k_in = 4) continuing each image's control and multiplier.  Timed: the batch with
+    CUDA graphs and autotuned tiles, the batch without graphs, the batch with the fixed
+    default tile, and the same work as one solve() per image in sequence.  With
+    tol_outer > 0 the whole batch is also solved to a relative residual of 1e-4 (at most
+    tol_outer multiplier steps) and the time to tolerance is reported."""
+    from synth import batch_specs, make_image
+    specs = batch_specs(count, 0)
+    if scale != 1.0:
+        from synth import ImageSpec
+        specs = [(ImageSpec(max(8, int(round(sp.height * scale))),
+                            max(8, int(round(sp.width * scale))), sp.channels,
+                            regions=sp.regions, ramp=sp.ramp, sigma=sp.sigma,
+                            spectral=sp.spectral), sd, r) for sp, sd, r in specs]
+    ctxs, eps, mus = [], [], []
+    stream = torch.cuda.Stream(device=dev)
+    pix = []
+    for sp, sd, r in specs:
+        img = torch.from_numpy(make_image(sp, sd).astype(np.float32)).to(dev)
+        p = lib.agents_default_params(sp.height, sp.width, sp.channels, r, BATCH_T)
+        ctxs.append(lib.Context(p, img, stream))
+        eps.append(torch.full((BATCH_T, 2), 57.0, dtype=torch.float64, device=dev))
+        mus.append(torch.zeros(sp.height, sp.width, 2, sp.channels, device=dev))
+        pix.append(sp.height * sp.width)
+    handles = [c.handle for c in ctxs]
+    torch.cuda.synchronize()
+
+    def work(infos):
+        return sum(n * (i.forward_steps + i.adjoint_steps + i.tv_sweeps)
+                   for n, i in zip(pix, infos))
+
+    def run_batch(o, autotune, graph):
+        return lib.agents_solve_batch(handles, o, eps, mus, None, autotune=autotune,
+                                      use_graph=graph)
+
+    def run_seq(o):
+        return [lib.solve(h, o, e, m) for h, e, m in zip(handles, eps, mus)]
+
+    def timed(fn, n):
+        ps = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            ps += work(fn())
+        torch.cuda.synchronize()
+        return ps, time.perf_counter() - t0
+
+    o = lib.agents_default_solve_opts()
+    o.k_out, o.k_in = 1, BATCH_K_IN
+    arms = {"graph_autotuned": lambda: run_batch(o, True, True),
+            "no_graph_autotuned": lambda: run_batch(o, True, False),
+            "graph_fixed_tile": lambda: run_batch(o, False, True),
+            "sequential_solve": lambda: run_seq(o)}
+    out = {}
+    for name, fn in arms.items():
+        for _ in range(warmup):
+            fn()
+        ps, t = timed(fn, steps)
+        out[name] = {"mpix_steps_per_s": ps / t / 1e6, "s_per_step": t / steps}
+    res = {"workload": (f"batch: {count} images, sides U{{128..1536}} x {scale:g}, aspect "
+                        f"U[0.5,2], 2/3 RGB + 1/3 31-band, R U{{3..7}}, T={BATCH_T}, "
+                        f"k_in={BATCH_K_IN}"),
+           "megapixels": sum(pix) / 1e6,
+           "channels": {"3": sum(1 for sp, _, _ in specs if sp.channels == 3),
+                        "31": sum(1 for sp, _, _ in specs if sp.channels == 31)},
+           "timing": "host wall clock around each call (the batch synchronises once per "
+                     "Armijo round), after warm-up",
+           **out}
+    if tol_outer > 0:
+        for e, m in zip(eps, mus):
+            e.fill_(57.0)
+            m.zero_()
+        ot = lib.agents_default_solve_opts()
+        ot.k_out, ot.k_in, ot.tol = tol_outer, 30, 1e-4
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = run_batch(ot, True, True)
+        torch.cuda.synchronize()
+        res["time_to_tol"] = {
+            "seconds": time.perf_counter() - t0, "tol": 1e-4, "k_out_max": tol_outer,
+            "k_in": 30, "converged": sum(1 for i in infos if i.final_res < 1e-4),
+            "outer_steps": [i.outer_done for i in infos]}
+    for c in ctxs:
+        c.close()
+    return res
+
+
 # ---------------------------------------------------------------- CPU oracle leg
 
 ORACLE_ROWS = 256
@@ -336,8 +431,15 @@ def main():
                     help="image side for the per-kernel roofline table (0: skip)")
     ap.add_argument("--kernel", default=None,
                     help="only time this kernel at --kernel-size and exit (profiling driver)")
-    ap.add_argument("--workload", default="throughput", choices=["throughput", "gradient"],
-                    help="gradient: the 2048^2, T=200 differentiation workload (own JSON line)")
+    ap.add_argument("--workload", default="throughput",
+                    choices=["throughput", "gradient", "batch"],
+                    help="gradient: the 2048^2, T=200 differentiation workload; batch: the "
+                         "uneven 96-image batch (each prints its own JSON line)")
+    ap.add_argument("--batch-count", type=int, default=96)
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="scale factor on the batch's image sides")
+    ap.add_argument("--batch-tol-outer", type=int, default=0,
+                    help="also solve the batch to 1e-4 with at most this many multiplier steps")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -364,6 +466,12 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     if args.workload == "gradient":
         res = gradient_workload(torch, lib, dev)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return 0
+    if args.workload == "batch":
+        res = batch_workload(torch, lib, dev, args.batch_count, args.batch_scale, args.steps,
+                             args.warmup, args.batch_tol_outer)
         if rank == 0:
             print(json.dumps(res), flush=True)
         return 0
