@@ -63,6 +63,12 @@ class agents_iter_record(ctypes.Structure):
                 ("gnorm2", c_double), ("tau", c_double)]
 
 
+class ws_net_config(ctypes.Structure):
+    _fields_ = [("in_ch", c_int32), ("out_ch", c_int32), ("base", c_int32),
+                ("levels", c_int32), ("nsteps", c_int32), ("eps_lo", ctypes.c_float * 2),
+                ("eps_hi", ctypes.c_float * 2)]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -91,6 +97,30 @@ _SIGNATURES = {
     "agents_solve_batch": (c_int, [c_int32, POINTER(c_void_p), POINTER(agents_solve_opts),
                                    c_int32, c_int32, POINTER(c_void_p), POINTER(c_void_p),
                                    POINTER(c_void_p), POINTER(agents_solve_info)]),
+    # warm-start network (include/warmstart.h)
+    "ws_last_error": (ctypes.c_char_p, []),
+    "ws_conv3x3_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                   c_int32, c_void_p]),
+    "ws_conv3x3_backward_data": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32,
+                                         c_int32, c_int32, c_int32, c_void_p]),
+    "ws_conv3x3_backward_weight": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                           c_int32, c_int32, c_int32, c_int32, c_int32,
+                                           c_void_p, ctypes.c_size_t, c_void_p]),
+    "ws_conv3x3_backward_weight_workspace": (ctypes.c_size_t, [c_int32, c_int32, c_int32,
+                                                               c_int32, c_int32]),
+    "ws_transpose_weights": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p]),
+    "ws_net_create": (c_int, [POINTER(ws_net_config), c_void_p, POINTER(c_void_p)]),
+    "ws_net_destroy": (None, [c_void_p]),
+    "ws_net_num_params": (ctypes.c_int64, [c_void_p]),
+    "ws_net_set_params": (c_int, [c_void_p, c_void_p]),
+    "ws_net_get_params": (c_int, [c_void_p, c_void_p]),
+    "ws_net_forward": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32,
+                               c_void_p, c_void_p, c_void_p]),
+    "ws_net_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
+                                 c_int32, ctypes.c_float, POINTER(c_double), c_void_p]),
+    "ws_net_adam_step": (c_int, [c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, ctypes.c_float]),
 }
 
 
@@ -300,3 +330,43 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- warm-start network
+def _ws_check(status: int, func: str):
+    if status != AGENTS_OK:
+        msg = load().ws_last_error()
+        raise AgentsError(status, func, msg.decode() if msg else "")
+
+
+def ws_conv3x3_forward(x, w16, bias, y, N, H, W, Cin, Cout, relu=True, up=False, add=None,
+                       y2=None, stream=None):
+    _ws_check(load().ws_conv3x3_forward(_ptr(x, "float32"), _ptr(w16), _ptr(bias, "float32"),
+                                        _ptr(y, "float32"), _ptr(add, "float32"),
+                                        _ptr(y2, "float32"), N, H, W, Cin, Cout, int(relu),
+                                        int(up), _stream(stream)), "ws_conv3x3_forward")
+
+
+def ws_conv3x3_backward_data(dy, wt16, dx, N, H, W, Cin, Cout, stream=None):
+    _ws_check(load().ws_conv3x3_backward_data(_ptr(dy, "float32"), _ptr(wt16), _ptr(dx, "float32"),
+                                              N, H, W, Cin, Cout, _stream(stream)),
+              "ws_conv3x3_backward_data")
+
+
+def ws_conv3x3_backward_weight_workspace(N, H, W, Cin, Cout) -> int:
+    return int(load().ws_conv3x3_backward_weight_workspace(N, H, W, Cin, Cout))
+
+
+def ws_conv3x3_backward_weight(x, dy, dw, db, N, H, W, Cin, Cout, workspace, up=False,
+                               stream=None):
+    nbytes = workspace.numel() * workspace.element_size()
+    _ws_check(load().ws_conv3x3_backward_weight(_ptr(x, "float32"), _ptr(dy, "float32"),
+                                                _ptr(dw, "float32"), _ptr(db, "float32"), N, H,
+                                                W, Cin, Cout, int(up), _ptr(workspace), nbytes,
+                                                _stream(stream)),
+              "ws_conv3x3_backward_weight")
+
+
+def ws_transpose_weights(w, w16, wt16, Cin, Cout, stream=None):
+    _ws_check(load().ws_transpose_weights(_ptr(w, "float32"), _ptr(w16), _ptr(wt16), Cin, Cout,
+                                          _stream(stream)), "ws_transpose_weights")

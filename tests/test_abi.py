@@ -12,6 +12,7 @@ from paper_2510_16154_gb300.build import build
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "agents.h")
+HEADERS = [HEADER, os.path.join(ROOT, "include", "warmstart.h")]
 
 
 @pytest.fixture(scope="module")
@@ -20,8 +21,8 @@ def cdll():
     return lib.load()
 
 
-def _declared_functions():
-    text = open(HEADER).read()
+def _declared_functions(headers=(HEADER,)):
+    text = "".join(open(h).read() for h in headers)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
                        text, flags=re.M)
@@ -36,7 +37,7 @@ def test_header_declares_the_six_entry_points():
 
 
 def test_library_exports_every_declared_symbol(cdll):
-    names = _declared_functions()
+    names = _declared_functions(HEADERS)
     assert len(names) >= 12
     for name in names:
         assert hasattr(cdll, name), name
@@ -96,3 +97,17 @@ def test_missing_library_fails_loudly(tmp_path):
             mod.load(str(tmp_path / "nope.so"))
         finally:
             mod._lib = saved
+
+
+def test_warmstart_config_layout_and_validation(cdll):
+    assert ctypes.sizeof(lib.ws_net_config) == 5 * 4 + 4 * 4
+    cfg = lib.ws_net_config()
+    cfg.in_ch, cfg.out_ch, cfg.base, cfg.levels, cfg.nsteps = 3, 6, 8, 1, 4   # levels < 2
+    cfg.eps_lo[0] = cfg.eps_lo[1] = 2.0
+    cfg.eps_hi[0] = cfg.eps_hi[1] = 1100.0
+    h = ctypes.c_void_p()
+    assert cdll.ws_net_create(ctypes.byref(cfg), None, ctypes.byref(h)) == lib.AGENTS_EINVAL
+    assert b"invalid configuration" in cdll.ws_last_error()
+    assert cdll.ws_conv3x3_forward(None, None, None, None, None, None, 1, 1, 1, 1, 1, 0, 0,
+                                   None) == lib.AGENTS_EINVAL
+    assert cdll.ws_conv3x3_backward_weight_workspace(2, 8, 8, 16, 32) > 0
