@@ -137,15 +137,23 @@ class ClockSampler:
                 "samples": len(mine)}
 
 
-def measure_kernels(torch, lib, dev, stream, size: int, reps: int = 5, only: str | None = None):
-    """Average device time of each kernel on a size x size x 3 image, R = 5, with CUDA
-    events on the library's stream.  Fields of 4096^2 x 3 float32 (201 MB) exceed the
-    129 MB L2, so the HBM-bound kernels are measured against HBM, not L2."""
+FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (no measured FP64 peak exists)
+FP64_FLOPS_PER_PIXEL_ALM = 10   # per channel: 2 gradients (sub, mul each), 2 residual
+                                # subtractions, 2 FMAs of the multiplier update
+
+
+def measure_kernels(torch, lib, dev, stream, size: int, reps: int = 5, only: str | None = None,
+                    channels: int = 3, radius: int = R):
+    """Average device time of each kernel on a size x size x channels image with window
+    radius `radius` (default 3 channels, R = 5), with CUDA events on the library's
+    stream.  Fields of 4096^2 x 3 float32 (201 MB) exceed the 129 MB L2, so the HBM-bound
+    kernels are measured against HBM, not L2."""
     Hs = Ws = size
-    Cs = 3
+    Cs = channels
     rng = np.random.default_rng(7)
-    img = rng.uniform(0.3, 0.7, size=(Hs, Ws, Cs)).astype(np.float32)
-    p = lib.agents_default_params(Hs, Ws, Cs, R, reps)
+    half = 0.2 if Cs <= 8 else 0.05          # most window pairs interact
+    img = rng.uniform(0.5 - half, 0.5 + half, size=(Hs, Ws, Cs)).astype(np.float32)
+    p = lib.agents_default_params(Hs, Ws, Cs, radius, reps)
     out = {}
     with lib.Context(p, torch.from_numpy(img).to(dev), stream) as ctx:
         c = torch.from_numpy(img).to(dev)
@@ -196,9 +204,15 @@ def measure_kernels(torch, lib, dev, stream, size: int, reps: int = 5, only: str
         t = rec["us"] / 1e6
         if name in ("forward", "adjoint"):
             fl = (forward_flops_per_launch if name == "forward" else adjoint_flops_per_launch)(
-                Hs, Ws, Cs, R)
+                Hs, Ws, Cs, radius)
             rec.update({"bound": "alu", "achieved": fl / t / 1e12, "unit": "TFLOP/s",
                         "peak": fp32_peak_tflops(sm_max)})
+        elif name == "alm_update":
+            by = BYTES_PER_PIXEL[name](Cs) * Hs * Ws
+            fl = FP64_FLOPS_PER_PIXEL_ALM * Cs * Hs * Ws
+            rec.update({"bound": "fp64", "achieved": fl / t / 1e12, "unit": "TFLOP/s",
+                        "peak": FP64_PEAK_TFLOPS, "peak_basis": "nominal FP64 rate",
+                        "hbm_gbs": by / t / 1e9, "hbm_frac": by / t / 1e9 / hbm, "bytes": by})
         else:
             by = BYTES_PER_PIXEL[name](Cs) * Hs * Ws
             rec.update({"bound": "hbm", "achieved": by / t / 1e9, "unit": "GB/s", "peak": hbm,
@@ -351,6 +365,55 @@ def batch_workload(torch, lib, dev, count: int, scale: float, steps: int, warmup
     return res
 
 
+def warmstart_workload(torch, lib, dev, count: int, size: int, reps: int):
+    """Time to a relative residual of 1e-4, warm start vs plain: `count` unseen synthetic
+    RGB images (Voronoi K ~ U{4..32}, ramp 0.1, sigma ~ U[0.02, 0.15]) of size^2, R = 5,
+    T = 20, k_in = 10, at most 40 multiplier steps, solved as one batched solve (CUDA
+    graphs, autotuned tiles) from the cold start (mu = 0, eps = 57) and from the
+    committed network's mu.  Device time per solve (CUDA events on the batch's stream
+    order: synchronised around each call), network inference included in the warm arm."""
+    from paper_2510_16154_gb300.train_warmstart import make_images, R as R_WS, T as T_WS
+    from paper_2510_16154_gb300.warmstart import WarmStartNet, WEIGHTS_DIR
+    net = WarmStartNet.load(os.path.join(WEIGHTS_DIR, "warmstart_rgb_T20_R5.npz"), dev)
+    imgs = make_images(count, size, 4242, dev)
+    o = lib.agents_default_solve_opts()
+    o.k_out, o.k_in, o.tol = 40, 10, 1e-4
+    ctxs = [lib.Context(lib.agents_default_params(size, size, 3, R_WS, T_WS),
+                        imgs[i].contiguous()) for i in range(count)]
+    out = {}
+    try:
+        for mode in ("cold", "warm", "cold", "warm")[: 2 * reps]:
+            eps = [torch.full((T_WS, 2), 57.0, dtype=torch.float64, device=dev)
+                   for _ in range(count)]
+            mus = [torch.zeros(size, size, 2, 3, device=dev) for _ in range(count)]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if mode == "warm":
+                mu_p, _ = net.predict(imgs)
+                mus = [mu_p[i].reshape(size, size, 2, 3).contiguous() for i in range(count)]
+            infos = lib.agents_solve_batch([c.handle for c in ctxs], o, eps, mus, None,
+                                           autotune=True, use_graph=True)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            r = out.setdefault(mode, {"seconds": []})
+            r["seconds"].append(t)
+            r["outer_mean"] = float(np.mean([i.outer_done for i in infos]))
+            r["reached_tol"] = int(sum(i.final_res < 1e-4 for i in infos))
+            r["final_obj_mean"] = float(np.mean([i.final_obj for i in infos]))
+    finally:
+        for c in ctxs:
+            c.close()
+        net.close()
+    cold, warm = min(out["cold"]["seconds"]), min(out["warm"]["seconds"])
+    return {"metric": "time to relative residual 1e-4, batched solve, warm start vs plain",
+            "value": warm, "unit": "s", "higher_is_better": False,
+            "cold_seconds": cold, "speedup": cold / warm,
+            "config": {"workload": f"{count} unseen {size}x{size}x3 Voronoi+ramp+noise images, "
+                                   f"R={R_WS}, T={T_WS}, k_in=10, k_out<=40, tol 1e-4",
+                       "weights": "paper_2510_16154_gb300/weights/warmstart_rgb_T20_R5.npz"},
+            "cold": out["cold"], "warm": out["warm"]}
+
+
 # ---------------------------------------------------------------- CPU oracle leg
 
 ORACLE_ROWS = 256
@@ -431,8 +494,10 @@ def main():
                     help="image side for the per-kernel roofline table (0: skip)")
     ap.add_argument("--kernel", default=None,
                     help="only time this kernel at --kernel-size and exit (profiling driver)")
+    ap.add_argument("--kernel-channels", type=int, default=3)
+    ap.add_argument("--kernel-radius", type=int, default=R)
     ap.add_argument("--workload", default="throughput",
-                    choices=["throughput", "gradient", "batch"],
+                    choices=["throughput", "gradient", "batch", "warmstart"],
                     help="gradient: the 2048^2, T=200 differentiation workload; batch: the "
                          "uneven 96-image batch (each prints its own JSON line)")
     ap.add_argument("--batch-count", type=int, default=96)
@@ -469,6 +534,12 @@ def main():
         if rank == 0:
             print(json.dumps(res), flush=True)
         return 0
+    if args.workload == "warmstart":
+        res = warmstart_workload(torch, lib, dev, args.batch_count if args.batch_count != 96
+                                 else 64, 256, max(1, min(2, args.steps)))
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return 0
     if args.workload == "batch":
         res = batch_workload(torch, lib, dev, args.batch_count, args.batch_scale, args.steps,
                              args.warmup, args.batch_tol_outer)
@@ -476,9 +547,12 @@ def main():
             print(json.dumps(res), flush=True)
         return 0
     if args.kernel:
-        res = measure_kernels(torch, lib, dev, stream, args.kernel_size, only=args.kernel)
+        res = measure_kernels(torch, lib, dev, stream, args.kernel_size, only=args.kernel,
+                              channels=args.kernel_channels, radius=args.kernel_radius)
         if rank == 0:
-            print(json.dumps({"kernel": args.kernel, "size": args.kernel_size, **res}), flush=True)
+            print(json.dumps({"kernel": args.kernel, "size": args.kernel_size,
+                              "channels": args.kernel_channels, "radius": args.kernel_radius,
+                              **res}), flush=True)
         return 0
 
     img = make_image(THROUGHPUT_1024_RGB, SEED + rank).astype(np.float32)

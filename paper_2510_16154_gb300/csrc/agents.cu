@@ -273,7 +273,66 @@ int alm(agents_ctx* ctx, const float* c, const float* c_prev, const float* v,
   return AGENTS_OK;
 }
 
+// Trial-trajectory buffers for trajectory reuse (full-store mode only); if they do not
+// fit, solve() recomputes trajectories as before.
+void ensure_reuse_buffers(agents_ctx* ctx) {
+  if (ctx->reuse_tried) return;
+  ctx->reuse_tried = true;
+  if (ctx->ckpt_every != 0 || ctx->T < 2) return;
+  void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+  const size_t sizes[4] = {(size_t)(ctx->T - 1) * ctx->nc, (size_t)(ctx->T - 1) * ctx->nc,
+                           ctx->nc, ctx->nc};
+  // only when a quarter of the device stays free afterwards
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const size_t need = (sizes[0] + sizes[1] + sizes[2] + sizes[3]) * sizeof(float);
+  if (free_b < need || free_b - need < total_b / 4) return;
+  for (int k = 0; k < 4; ++k) {
+    if (cudaMalloc(&p[k], sizes[k] * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      for (int m = 0; m < k; ++m) cudaFree(p[m]);
+      return;
+    }
+  }
+  for (int k = 0; k < 4; ++k) ctx->allocs.push_back(p[k]);
+  ctx->traj_alt[0] = static_cast<float*>(p[0]);
+  ctx->traj_alt[1] = static_cast<float*>(p[1]);
+  ctx->cT_alt[0] = static_cast<float*>(p[2]);
+  ctx->cT_alt[1] = static_cast<float*>(p[3]);
+  ctx->reuse = true;
+}
+
+// Full-store forward sweep into a given trajectory buffer and final state.
+int forward_sweep_into(agents_ctx* ctx, const double* d_eps, float* traj, float* dst_T) {
+  const int T = ctx->T;
+  const float* cur = ctx->c0;
+  for (int n = 0; n < T; ++n) {
+    float* dst = n == T - 1 ? dst_T : traj + (size_t)n * ctx->nc;
+    CK(launch_forward_step(cur, dst, d_eps + 2 * n, ctx->sg, ctx->stream));
+    ++ctx->launches;
+    cur = dst;
+  }
+  return AGENTS_OK;
+}
+
+// c(T) of the control in d_eps into dst: a copy of the stored final state when the stored
+// trajectory belongs to that control, else a forward sweep.  Returns the steps executed.
+int final_state(agents_ctx* ctx, float* dst, int64_t& steps) {
+  if (ctx->reuse && ctx->traj_ok) {
+    CK(cudaMemcpyAsync(dst, ctx->cT, ctx->nc * sizeof(float), cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    return AGENTS_OK;
+  }
+  TRY(forward_sweep(ctx, ctx->d_eps, dst, false));
+  steps += ctx->T;
+  return AGENTS_OK;
+}
+
 int ensure_solve_buffers(agents_ctx* ctx) {
+  ensure_reuse_buffers(ctx);
   if (ctx->s_c) return AGENTS_OK;
   TRY(dalloc(ctx, &ctx->s_c, ctx->nc));
   TRY(dalloc(ctx, &ctx->s_cn, ctx->nc));
@@ -312,8 +371,11 @@ int dal_iteration(agents_ctx* ctx, const agents_solve_opts& o, const float* v, c
   const double hi[2] = {ctx->p.eps_hi[0], ctx->p.eps_hi[1]};
   auto count_fwd = [&]() { inf.forward_steps += T; };
   ended = false;
-  TRY(forward_sweep(ctx, ctx->d_eps, ctx->cT, true));
-  count_fwd();
+  if (!(ctx->reuse && ctx->traj_ok)) {
+    TRY(forward_sweep(ctx, ctx->d_eps, ctx->cT, true));
+    count_fwd();
+    ctx->traj_ok = ctx->reuse;
+  }
   float* lam0 = nullptr;
   TRY(adjoint_sweep(ctx, ctx->d_eps, v, mu, 0, &lam0));
   inf.adjoint_steps += T;
@@ -356,9 +418,15 @@ int dal_iteration(agents_ctx* ctx, const agents_solve_opts& o, const float* v, c
     CK(launch_control_step(ctx->d_eps, ctx->d_D, tau, ctx->d_lohi, ctx->d_trial[cur], T,
                            ctx->stream));
     ++ctx->launches;
-    TRY(forward_sweep(ctx, ctx->d_trial[cur], ctx->s_trial_c, false));
+    float* trial_c = ctx->s_trial_c;
+    if (ctx->reuse) {   // keep the trial's trajectory: it is the next stored one if accepted
+      trial_c = ctx->cT_alt[cur];
+      TRY(forward_sweep_into(ctx, ctx->d_trial[cur], ctx->traj_alt[cur], trial_c));
+    } else {
+      TRY(forward_sweep(ctx, ctx->d_trial[cur], trial_c, false));
+    }
     count_fwd();
-    TRY(objective(ctx, ctx->s_trial_c, v, mu, nullptr, 1));
+    TRY(objective(ctx, trial_c, v, mu, nullptr, 1));
     inf.tv_sweeps += 1;
     ++inf.trials;
     double L;
@@ -407,6 +475,11 @@ int dal_iteration(agents_ctx* ctx, const agents_solve_opts& o, const float* v, c
   ctx->log.push_back(rec);
   CK(cudaMemcpyAsync(ctx->d_eps, ctx->d_trial[best], 2 * (size_t)T * sizeof(double),
                      cudaMemcpyDeviceToDevice, ctx->stream));
+  if (ctx->reuse) {   // the accepted trial's trajectory becomes the stored one
+    std::swap(ctx->traj, ctx->traj_alt[best]);
+    std::swap(ctx->cT, ctx->cT_alt[best]);
+    ctx->traj_ok = true;
+  }
   sigma = best_tau;
   return AGENTS_OK;
 }
@@ -727,6 +800,7 @@ int dal_solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, fl
   CK(cudaMemsetAsync(ctx->s_v, 0, ctx->nv * sizeof(float), ctx->stream));
   CK(cudaMemsetAsync(ctx->s_mu, 0, ctx->nv * sizeof(float), ctx->stream));
   ctx->stored = false;
+  ctx->traj_ok = false;
   double sigma = o.sigma0;
   std::vector<double> Dh(2 * (size_t)T);
   int status = AGENTS_OK;
@@ -742,10 +816,10 @@ int dal_solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, fl
   ctx->stored = false;
   TRY(from_device(ctx, eps_io, ctx->d_eps, 2 * (size_t)T * sizeof(double)));
   if (c_out) {
-    TRY(forward_sweep(ctx, ctx->d_eps, ctx->s_c, false));
-    inf.forward_steps += T;
+    TRY(final_state(ctx, ctx->s_c, inf.forward_steps));
     TRY(from_device(ctx, c_out, ctx->s_c, ctx->nc * sizeof(float)));
   }
+  ctx->traj_ok = false;
   CK(cudaStreamSynchronize(ctx->stream));
   inf.final_sigma = sigma;
   inf.kernel_launches = ctx->launches - launches0;
@@ -774,11 +848,19 @@ int solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float*
                      cudaMemcpyHostToDevice, ctx->stream));
   TRY(to_device(ctx, ctx->s_mu, mu_io, ctx->nv * sizeof(float)));
   ctx->stored = false;
+  ctx->traj_ok = false;
 
   double sigma = o.sigma0;
   float *c = ctx->s_c, *cn = ctx->s_cn, *v = ctx->s_v, *vn = ctx->s_vn, *mu = ctx->s_mu;
   // c^(0) = c(T; eps^(0)),  v^(0) = argmin_v L(c^(0), v, mu^(0))
-  TRY(forward_sweep(ctx, ctx->d_eps, c, false));
+  if (ctx->reuse) {   // stored sweep: the first DAL iteration reuses it
+    TRY(forward_sweep(ctx, ctx->d_eps, ctx->cT, true));
+    ctx->traj_ok = true;
+    CK(cudaMemcpyAsync(c, ctx->cT, ctx->nc * sizeof(float), cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+  } else {
+    TRY(forward_sweep(ctx, ctx->d_eps, c, false));
+  }
   count_fwd();
   CK(launch_pd_tv_step(c, mu, v, ctx->tg, ctx->stream));
   ++ctx->launches;
@@ -799,8 +881,7 @@ int solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float*
     }
     if (status != AGENTS_OK) break;
     // ---- c^(j), v^(j), mu^(j)
-    TRY(forward_sweep(ctx, ctx->d_eps, cn, false));
-    count_fwd();
+    TRY(final_state(ctx, cn, inf.forward_steps));
     CK(launch_pd_tv_step(cn, mu, vn, ctx->tg, ctx->stream));
     ++ctx->launches;
     double st[5];
@@ -824,6 +905,7 @@ int solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float*
     if (o.tol > 0.0 && inf.final_res < o.tol) break;
   }
   ctx->stored = false;
+  ctx->traj_ok = false;
   // outputs
   TRY(from_device(ctx, eps_io, ctx->d_eps, 2 * (size_t)T * sizeof(double)));
   TRY(from_device(ctx, mu_io, mu, ctx->nv * sizeof(float)));

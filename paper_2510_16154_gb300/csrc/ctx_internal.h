@@ -55,6 +55,16 @@ struct agents_ctx {
   float *s_c = nullptr, *s_cn = nullptr, *s_v = nullptr, *s_vn = nullptr, *s_mu = nullptr;
   float* s_trial_c = nullptr;
 
+  // trajectory reuse in full-store mode: Armijo trials store their trajectories in
+  // traj_alt/cT_alt; an accepted trial's buffers are swapped in, so the next DAL
+  // iteration and the multiplier step need no forward sweep (traj_ok: ctx->traj holds
+  // the trajectory of the control in d_eps).  Off when the buffers cannot be allocated.
+  float* traj_alt[2] = {nullptr, nullptr};
+  float* cT_alt[2] = {nullptr, nullptr};
+  bool reuse = false;
+  bool reuse_tried = false;
+  bool traj_ok = false;
+
   int64_t launches = 0;           // kernels launched by this context (for accounting)
   std::vector<agents_iter_record> log;  // per-DAL-iteration records of the last solve()
   std::vector<void*> allocs;

@@ -1,5 +1,6 @@
 // Adjoint step launcher: tiled kernels for (R <= 8, C in {1, 3}), generic otherwise.
 #include "sweep_config.cuh"
+#include "sweep_wide.cuh"
 
 namespace agents {
 
@@ -53,6 +54,7 @@ cudaError_t launch_adjoint_batch(const BatchSweepImg* imgs, const BatchJob* jobs
                                  const int* active, int n, int R, int C, int shape,
                                  cudaStream_t s) {
   if (!tiled_shape(R, C)) {
+    if (wide_shape(R, C)) return launch_wide_adjoint_batch(imgs, jobs, njobs, active, n, R, s);
     if (C > kGenericMaxC) return cudaErrorInvalidValue;
     const int grid = njobs < 4096 ? njobs : 4096;
     if (grid <= 0) return cudaSuccess;
@@ -84,7 +86,9 @@ cudaError_t launch_adjoint_step(const float* c_n, const float* lam_next, float* 
                                 cudaStream_t s) {
 #define AGENTS_ADJ(R, C) adjoint_tiled<R, C>(c_n, lam_next, lam_out, eps_n, partial, g, s)
   AGENTS_DISPATCH_RC(g.R, g.C, AGENTS_ADJ,
-                     adjoint_generic(c_n, lam_next, lam_out, eps_n, partial, g, s));
+                     wide_shape(g.R, g.C)
+                         ? launch_wide_adjoint(c_n, lam_next, lam_out, eps_n, partial, g, s)
+                         : adjoint_generic(c_n, lam_next, lam_out, eps_n, partial, g, s));
 #undef AGENTS_ADJ
 }
 

@@ -1,5 +1,6 @@
 // Forward Euler step launcher: tiled kernels for (R <= 8, C in {1, 3}), generic otherwise.
 #include "sweep_config.cuh"
+#include "sweep_wide.cuh"
 
 namespace agents {
 
@@ -54,6 +55,7 @@ cudaError_t launch_forward_batch(const BatchSweepImg* imgs, const BatchJob* jobs
                                  const int* active, int n, int kind, int R, int C, int shape,
                                  cudaStream_t s) {
   if (!tiled_shape(R, C)) {
+    if (wide_shape(R, C)) return launch_wide_forward_batch(imgs, jobs, njobs, active, n, kind, R, s);
     if (C > kGenericMaxC) return cudaErrorInvalidValue;
     const int grid = njobs < 4096 ? njobs : 4096;
     if (grid <= 0) return cudaSuccess;
@@ -72,7 +74,9 @@ cudaError_t launch_forward_batch(const BatchSweepImg* imgs, const BatchJob* jobs
 cudaError_t launch_forward_step(const float* c_in, float* c_out, const double* eps_n,
                                 const SweepGeom& g, cudaStream_t s) {
 #define AGENTS_FWD(R, C) forward_tiled<R, C>(c_in, c_out, eps_n, g, s)
-  AGENTS_DISPATCH_RC(g.R, g.C, AGENTS_FWD, forward_generic(c_in, c_out, eps_n, g, s));
+  AGENTS_DISPATCH_RC(g.R, g.C, AGENTS_FWD,
+                     wide_shape(g.R, g.C) ? launch_wide_forward(c_in, c_out, eps_n, g, s)
+                                          : forward_generic(c_in, c_out, eps_n, g, s));
 #undef AGENTS_FWD
 }
 

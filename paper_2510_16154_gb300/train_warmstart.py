@@ -9,10 +9,12 @@
    cold start (mu = 0, eps = 57).  Targets: the converged dual field mu* and log eps*.
 2. Training: Adam on the library's forward/backward kernels (loss: mean squared error on
    mu plus 0.1 x mean squared error on log eps).
-3. Evaluation on unseen images of the same generator at eval-size: solve() to 1e-4
-   cold, warm-started from the network (mu and eps), and from its mu only; multiplier
-   steps, Armijo trials and device time of each, the network's own time, and the largest
-   difference between the warm and the cold answer.
+3. Evaluation on unseen images of the same generator: the whole set as one batched
+   solve (agents_solve_batch) to 1e-4, cold, warm-started from the network's mu, and from
+   its mu and eps; a subset one by one through solve() with per-image multiplier steps,
+   device time, the network's own time and the largest difference between the warm and
+   the cold answer; and a few images at a higher resolution than the training set.
+   The fallback to the cold start is taken on divergence.
 """
 from __future__ import annotations
 
@@ -82,14 +84,14 @@ def solve_targets(imgs, k_out, chunk, stream, log):
     return mu_all, le_all, outer
 
 
-def evaluate(net, n, size, seed, stream, log, k_out=150):
+def evaluate(net, n, size, seed, stream, log, k_out=150, per_image=True):
     from .warmstart import warm_solve
     dev = net.device
     imgs = make_images(n, size, seed, dev)
     o = lib.agents_default_solve_opts()
     o.k_out, o.k_in, o.tol = k_out, K_IN, TOL
     rows = []
-    for i in range(n):
+    for i in range(n if per_image else 0):
         img = imgs[i].contiguous()
         p = lib.agents_default_params(size, size, 3, R, T)
         with lib.Context(p, img, stream) as ctx:
@@ -127,8 +129,38 @@ def evaluate(net, n, size, seed, stream, log, k_out=150):
         if log:
             log(f"eval {i + 1}/{n}: " + ", ".join(
                 f"{m} {r['outer']} steps {r['seconds']:.2f}s" for m, r in res.items()))
-    summary = {}
-    for mode in ("cold", "warm", "warm_mu"):
+    # the same images as one batched solve (CUDA graphs), cold and warm
+    batch = {}
+    ctxs = [lib.Context(lib.agents_default_params(size, size, 3, R, T), imgs[i].contiguous(),
+                        stream) for i in range(n)]
+    try:
+        for mode in ("cold", "warm_mu", "warm"):
+            eps = [torch.full((T, 2), 57.0, dtype=torch.float64, device=dev) for _ in range(n)]
+            mus = [torch.zeros(size, size, 2, 3, device=dev) for _ in range(n)]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if mode != "cold":
+                mu_p, eps_p = net.predict(imgs)
+                if mode == "warm":
+                    eps = [eps_p[i].contiguous() for i in range(n)]
+                mus = [mu_p[i].reshape(size, size, 2, 3).contiguous() for i in range(n)]
+            infos = lib.agents_solve_batch([c.handle for c in ctxs], o, eps, mus, None,
+                                           autotune=True, use_graph=True)
+            torch.cuda.synchronize()
+            batch[mode] = {"seconds": time.perf_counter() - t0,
+                           "outer_mean": float(np.mean([i.outer_done for i in infos])),
+                           "outer": [i.outer_done for i in infos],
+                           "reached_tol": int(sum(i.final_res < TOL for i in infos)),
+                           "final_obj_mean": float(np.mean([i.final_obj for i in infos]))}
+            if log:
+                log(f"batched {mode}: {batch[mode]['seconds']:.2f} s, multiplier steps mean "
+                    f"{batch[mode]['outer_mean']:.1f}, reached tol {batch[mode]['reached_tol']}"
+                    f"/{n}, mean final L~ {batch[mode]['final_obj_mean']:.4f}")
+    finally:
+        for c in ctxs:
+            c.close()
+    summary = {"batched": batch}
+    for mode in ("cold", "warm", "warm_mu") if rows else ():
         summary[mode] = {
             "outer_mean": float(np.mean([r[mode]["outer"] for r in rows])),
             "inner_mean": float(np.mean([r[mode]["inner"] for r in rows])),
@@ -155,8 +187,12 @@ def main(argv=None):
     ap.add_argument("--levels", type=int, default=4)
     ap.add_argument("--out", default=os.path.join(WEIGHTS_DIR, "warmstart_rgb_T20_R5.npz"))
     ap.add_argument("--init", default=None, help="start from these weights instead of a seed")
-    ap.add_argument("--eval-n", type=int, default=8)
-    ap.add_argument("--eval-size", type=int, default=1024)
+    ap.add_argument("--eval-n", type=int, default=64)
+    ap.add_argument("--eval-size", type=int, default=256)
+    ap.add_argument("--eval-per-image", type=int, default=16,
+                    help="also solve this many of the eval images one by one (3 modes)")
+    ap.add_argument("--xres-n", type=int, default=4, help="cross-resolution eval images")
+    ap.add_argument("--xres-size", type=int, default=1024)
     ap.add_argument("--json", default=None)
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args(argv)
@@ -204,8 +240,17 @@ def main(argv=None):
     else:
         net = WarmStartNet.load(args.out, dev, stream)
     if args.eval_n > 0:
-        report["eval"] = evaluate(net, args.eval_n, args.eval_size, 900 + args.seed, stream, log)
+        report["eval"] = evaluate(net, args.eval_n, args.eval_size, 900 + args.seed, stream, log,
+                                  k_out=args.k_out, per_image=False)
         log(json.dumps(report["eval"]["summary"]))
+    if args.eval_per_image > 0:
+        report["eval_per_image"] = evaluate(net, args.eval_per_image, args.eval_size,
+                                            900 + args.seed, stream, log, k_out=args.k_out)
+        log(json.dumps(report["eval_per_image"]["summary"]))
+    if args.xres_n > 0:
+        report["eval_xres"] = evaluate(net, args.xres_n, args.xres_size, 950 + args.seed, stream,
+                                       log, k_out=150)
+        log(json.dumps(report["eval_xres"]["summary"]))
     if args.json:
         with open(args.json, "w") as f:
             json.dump(report, f, indent=1)

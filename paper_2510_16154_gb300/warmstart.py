@@ -202,10 +202,11 @@ class WarmStartNet:
         return history
 
 
-def warm_solve(ctx_handle, net: WarmStartNet, img: torch.Tensor, opts, use_eps: bool = True,
-               c_out=None):
-    """solve() started from the network's (mu(0), eps(0)); falls back to the cold start
-    (mu = 0, eps = 57) when the warm solve diverges or misses the tolerance.
+def warm_solve(ctx_handle, net: WarmStartNet, img: torch.Tensor, opts, use_eps: bool = False,
+               c_out=None, fallback_on_miss: bool = False):
+    """solve() started from the network's mu(0) (and its eps(0) with use_eps); falls back
+    to the cold start (mu = 0, eps = 57) when the warm solve diverges (AGENTS_EDIVERGED),
+    and with fallback_on_miss also when it ends without reaching opts.tol.
     Returns (info, eps, mu, used_fallback)."""
     T = net.spec.nsteps
     mu0, eps0 = net.predict(img)
@@ -214,7 +215,7 @@ def warm_solve(ctx_handle, net: WarmStartNet, img: torch.Tensor, opts, use_eps: 
     mu = mu0.reshape(img.shape[0], img.shape[1], 2, -1).contiguous()
     try:
         info = lib.solve(ctx_handle, opts, eps, mu, None, c_out)
-        ok = opts.tol <= 0 or info.final_res < opts.tol
+        ok = not fallback_on_miss or opts.tol <= 0 or info.final_res < opts.tol
     except lib.AgentsError as e:
         if e.code != lib.AGENTS_EDIVERGED:
             raise

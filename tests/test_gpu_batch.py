@@ -17,13 +17,13 @@ pytestmark = pytest.mark.gpu
 
 CASES = [  # (H, W, C, R, regions, seed)
     (40, 56, 3, 2, 4, 1), (23, 70, 3, 3, 3, 2), (64, 33, 1, 2, 5, 3), (17, 19, 3, 2, 2, 4),
-    (31, 45, 5, 2, 3, 5), (48, 48, 3, 3, 6, 6),
+    (31, 45, 5, 2, 3, 5), (48, 48, 3, 3, 6, 6), (22, 37, 31, 3, 3, 7), (18, 30, 31, 5, 2, 8),
 ]
 T = 6
 
 
 def _image(H, W, C, K, seed):
-    if C == 5:
+    if C > 3:
         return f32(make_image(ImageSpec(H, W, C, regions=K, sigma=0.05, spectral=True), seed))
     return f32(make_image(ImageSpec(H, W, C, regions=K, sigma=0.05), seed))
 
@@ -73,8 +73,10 @@ def test_batch_is_bitwise_equal_to_single_solves(use_graph, alpha):
         assert np.array_equal(mu_b[k], mu), k
         assert np.array_equal(c_b[k], c), k
         assert infos[k].trials == info.trials and infos[k].outer_done == info.outer_done
-        assert infos[k].forward_steps == info.forward_steps
+        assert infos[k].inner_done == info.inner_done
         assert infos[k].adjoint_steps == info.adjoint_steps
+        # solve() reuses accepted trial trajectories; the batch recomputes them
+        assert info.forward_steps <= infos[k].forward_steps
 
 
 def test_batch_tolerance_stops_images_independently():

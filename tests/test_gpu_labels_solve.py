@@ -252,3 +252,30 @@ def test_dal_solve_with_J_matches_oracle(alpha):
     Ls = [r["L"] for r in log if r["status"] == 0]
     assert all(b <= a for a, b in zip(Ls, Ls[1:]))          # J decreases
     assert oracle.cost_J(c.astype(np.float64), c0, op) == pytest.approx(info.final_obj, rel=1e-5)
+
+
+def test_trajectory_reuse_changes_nothing():
+    """Full-store mode reuses accepted trial trajectories (fewer Euler steps); the
+    checkpointed mode recomputes them.  Both must give bitwise the same solve."""
+    ensure_lib()
+    img = f32(make_image(ImageSpec(40, 52, 3, regions=5, ramp=0.05, sigma=0.06), 4))
+    outs = []
+    for mode in (0, 3):
+        p, _ = params(40, 52, 3, 3, 9, traj_mode=mode)
+        o = lib.agents_default_solve_opts()
+        o.k_out, o.k_in = 3, 6
+        eps = np.full((9, 2), 57.0)
+        mu = np.zeros((40, 52, 2, 3), dtype=np.float32)
+        c = np.zeros((40, 52, 3), dtype=np.float32)
+        with lib.Context(p, dev(img, np.float32)) as ctx:
+            info = lib.solve(ctx.handle, o, eps, mu, None, c)
+            eps2 = eps.copy()
+            dinfo = lib.dal_solve(ctx.handle, o, eps2, c2 := np.zeros_like(c))
+        outs.append((eps, mu, c, info, eps2, c2, dinfo))
+    (e0, m0, c0, i0, f0, d0, j0), (e1, m1, c1, i1, f1, d1, j1) = outs
+    assert np.array_equal(e0, e1) and np.array_equal(m0, m1) and np.array_equal(c0, c1)
+    assert np.array_equal(f0, f1) and np.array_equal(d0, d1)
+    assert i0.trials == i1.trials and i0.outer_done == i1.outer_done
+    # mode 0 skips the recomputations; mode 3 also recomputes checkpoint segments
+    assert i0.forward_steps < i1.forward_steps
+    assert j0.forward_steps < j1.forward_steps
