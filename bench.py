@@ -365,6 +365,65 @@ def batch_workload(torch, lib, dev, count: int, scale: float, steps: int, warmup
     return res
 
 
+def warmstart_net_flops(spec, n, h, w):
+    """Algorithmic flops of one forward pass of the warm-start network (convolutions only,
+    FMA = 2): sum over convolutions of 2 * 9 * Cin * Cout * pixels of its level."""
+    total = 0
+    for name, shape in spec.param_shapes():
+        if not name.endswith(".W"):
+            continue
+        cout, _, _, cin = shape
+        lvl = int(name[3]) if name[:3] in ("enc", "dec") else 1
+        total += 2 * 9 * cin * cout * n * (h >> (lvl - 1)) * (w >> (lvl - 1))
+    return total
+
+
+def measure_warmstart_net(torch, lib, dev, size: int, reps: int = 5):
+    """Device time of the warm-start network: inference on one size x size image and one
+    training step (forward, backward, Adam) on 16 images of 256 x 256; tensor-core
+    throughput against the measured bf16 peak (convolution flops; backward = 2 x
+    forward)."""
+    from paper_2510_16154_gb300.warmstart import WarmStartNet, WEIGHTS_DIR
+    net = WarmStartNet.load(os.path.join(WEIGHTS_DIR, "warmstart_rgb_T20_R5.npz"), dev)
+    g = torch.Generator(device=dev).manual_seed(3)
+    img = torch.rand(1, size, size, 3, device=dev, generator=g)
+    xb = torch.rand(16, 256, 256, 3, device=dev, generator=g)
+    mt = torch.randn(16, 256, 256, 6, device=dev, generator=g) * 0.3
+    le = torch.full((16, 2 * net.spec.nsteps), 4.0, device=dev)
+    theta = net.get_params()
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / n
+
+    t_inf = timed(lambda: net.predict(img), reps)
+
+    def train_step():
+        net.loss_grad(xb, mt, le)
+        net.adam_step(1e-4)
+
+    t_train = timed(train_step, reps)
+    net.set_params(theta)
+    net.close()
+    peak = float(load_peaks().get("bf16_tflops", 1899.9))
+    f_inf = warmstart_net_flops(net.spec, 1, size, size)
+    f_train = 3 * warmstart_net_flops(net.spec, 16, 256, 256)
+    return {"inference": {"size": size, "ms": t_inf * 1e3, "tflops": f_inf / t_inf / 1e12,
+                          "frac": f_inf / t_inf / 1e12 / peak},
+            "train_step": {"batch": "16 x 256 x 256", "ms": t_train * 1e3,
+                           "tflops": f_train / t_train / 1e12,
+                           "frac": f_train / t_train / 1e12 / peak},
+            "peak": peak, "peak_basis": "measured bf16 cuBLAS burst (MEASURED_PEAKS.json)",
+            "bound": "tensor"}
+
+
 def warmstart_workload(torch, lib, dev, count: int, size: int, reps: int):
     """Time to a relative residual of 1e-4, warm start vs plain: `count` unseen synthetic
     RGB images (Voronoi K ~ U{4..32}, ramp 0.1, sigma ~ U[0.02, 0.15]) of size^2, R = 5,
@@ -546,6 +605,11 @@ def main():
         if rank == 0:
             print(json.dumps(res), flush=True)
         return 0
+    if args.kernel == "warmstart_net":
+        res = measure_warmstart_net(torch, lib, dev, args.kernel_size)
+        if rank == 0:
+            print(json.dumps({"kernel": args.kernel, **res}), flush=True)
+        return 0
     if args.kernel:
         res = measure_kernels(torch, lib, dev, stream, args.kernel_size, only=args.kernel,
                               channels=args.kernel_channels, radius=args.kernel_radius)
@@ -637,8 +701,15 @@ def main():
     peaks = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(sm_max)
+    # DRAM traffic of this kernel from ncu at 4096 x 4096 x 3 (fields larger than L2; see
+    # profiles/forward_tile_kernel_4096x4096x3_R5.md): 201.35 MB read + 158.56 MB written
+    # per launch, scaled by pixels to this launch; at 1024^2 the fields fit in L2, so the
+    # launch's own DRAM traffic is at most this.
+    traffic = (201.348864e6 + 158.556416e6) * (H * W) / (4096 * 4096)
     roofline = {"bound": "alu", "kernel": "forward_tile_kernel<5,3>", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_basis": "ncu dram bytes at 4096x4096x3 scaled by pixels",
+                "algorithmic_bytes": 8 * C * H * W,
                 "peak_basis": f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (max SM clock)",
                 "launch_us": launch_s * 1e6,
                 "flops_per_launch": flops}

@@ -201,8 +201,14 @@ void agents_default_solve_opts(agents_solve_opts* o);
  * of each class by timing (cached per process); with autotune = 0 every image's result is
  * bitwise that of solve().  eps_io[i], mu_io[i] (host or device) as in solve(); c_out[i]
  * (host or device, may be NULL, or c_out itself NULL); infos: host array of n records
- * (may be NULL; kernel_launches is -1, launches being shared by the batch).  Work is
- * ordered after the first context's stream; the call returns when it is done. */
+ * (may be NULL; kernel_launches is -1, launches being shared by the batch; forward_steps
+ * counts every recomputed sweep).  Work is ordered after the first context's stream; the
+ * call returns when it is done.  Returns AGENTS_EINVAL for n < 1, NULL contexts or
+ * buffers, invalid opts, mixed nsteps or devices, or a checkpointed context;
+ * AGENTS_EDIVERGED when an image's objective became NaN/Inf (that image stops, the others
+ * finish and every output is written); AGENTS_ECUDA / AGENTS_ENOMEM with the message in
+ * agents_last_error(ctxs[0]).  The paper solves one image at a time; this is its solve
+ * applied to many images in one pass. */
 int agents_solve_batch(int32_t n, agents_ctx* const* ctxs, const agents_solve_opts* opts,
                        int32_t autotune, int32_t use_graph, double* const* eps_io,
                        float* const* mu_io, float* const* c_out, agents_solve_info* infos);

@@ -1,6 +1,6 @@
 """GPU checks of the learned warm start with the committed weights
 (paper_2510_16154_gb300/weights/warmstart_rgb_T20_R5.npz, trained by train_warmstart on
-1536 method-generated solves of 256 x 256 images).
+4000 method-generated solves of 256 x 256 images).
 
 * On unseen images of the training generator, the batched solve started from the
   network's mu needs fewer multiplier steps to the relative residual 1e-4 than the cold
