@@ -230,6 +230,26 @@ typedef struct {
 int agents_solve_log(const agents_ctx* ctx, agents_iter_record* out, int32_t capacity,
                      int32_t* count);
 
+/* One record per multiplier step of the last solve() on a context: the Section 4.1
+ * quantities the stopping test and the convergence plots use. */
+typedef struct {
+  int32_t outer;       /* multiplier step j (1-based)                                     */
+  int32_t inner_done;  /* DAL iterations of this step's eps-step                          */
+  double L;            /* L~(c^j, v^j, mu^j)                                              */
+  double K;            /* K(c^j) = dx dy sum_i [|(G c^j)_i| + alpha/2 |c^j_i - c0_i|^2]   */
+  double r;            /* |v^j - G c^j|                                                   */
+  double s;            /* rho |G^T (v^j - v^{j-1})|                                       */
+  double gap;          /* gamma dx dy |v^j - G c^j|^2                                     */
+  double rel_dc;       /* |c^j - c^{j-1}| / |c^j|                                         */
+  double res;          /* max(rel_dc, |L~_j - L~_{j-1}| / |L~_{j-1}|)                     */
+  double sigma;        /* Armijo step carried into the next DAL iteration                 */
+} agents_outer_record;
+
+/* Copy up to `capacity` multiplier-step records of the last solve() into out (host);
+ * *count receives the number available; out may be NULL to query the count. */
+int agents_solve_outer_log(const agents_ctx* ctx, agents_outer_record* out, int32_t capacity,
+                           int32_t* count);
+
 /* Algorithm 1 on its own (Section 3): the direct-adjoint loop with projected two-way
  * Armijo search on the terminal cost L~(c(T), 0, 0) = dx dy sum_i [rho/2 |G c_i|^2 +
  * alpha/2 |c_i - c0_i|^2], which is J of Eq. cost_functional when the context was created

@@ -63,6 +63,12 @@ class agents_iter_record(ctypes.Structure):
                 ("gnorm2", c_double), ("tau", c_double)]
 
 
+class agents_outer_record(ctypes.Structure):
+    _fields_ = [("outer", c_int32), ("inner_done", c_int32), ("L", c_double), ("K", c_double),
+                ("r", c_double), ("s", c_double), ("gap", c_double), ("rel_dc", c_double),
+                ("res", c_double), ("sigma", c_double)]
+
+
 class ws_net_config(ctypes.Structure):
     _fields_ = [("in_ch", c_int32), ("out_ch", c_int32), ("base", c_int32),
                 ("levels", c_int32), ("nsteps", c_int32), ("eps_lo", ctypes.c_float * 2),
@@ -87,6 +93,7 @@ _SIGNATURES = {
     "alm_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "agents_labels": (c_int, [c_void_p, c_void_p, c_float, c_void_p, c_void_p]),
     "agents_solve_log": (c_int, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
+    "agents_solve_outer_log": (c_int, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
     "agents_objective_noalloc": (c_int, [c_int32, c_int32, c_int32, c_double, c_double, c_int32,
                                          c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p]),
@@ -294,6 +301,31 @@ def agents_solve_log(ctx):
     _check(load().agents_solve_log(ctx, buf, n.value, ctypes.byref(n)), "agents_solve_log", ctx)
     return [{f: getattr(buf[i], f) for f, _ in agents_iter_record._fields_ if f != "reserved"}
             for i in range(n.value)]
+
+
+def agents_solve_outer_log(ctx):
+    """Per-multiplier-step records of the last solve() as a list of dicts."""
+    n = c_int32(0)
+    _check(load().agents_solve_outer_log(ctx, None, 0, ctypes.byref(n)),
+           "agents_solve_outer_log", ctx)
+    buf = (agents_outer_record * max(n.value, 1))()
+    _check(load().agents_solve_outer_log(ctx, buf, n.value, ctypes.byref(n)),
+           "agents_solve_outer_log", ctx)
+    return [{f: getattr(buf[i], f) for f, _ in agents_outer_record._fields_}
+            for i in range(n.value)]
+
+
+def write_solve_log_jsonl(ctx, path, info=None):
+    """Write the last solve()'s logs as JSON lines: one {"kind": "dal", ...} line per DAL
+    iteration, one {"kind": "outer", ...} line per multiplier step, and the solve_info."""
+    import json
+    with open(path, "w") as f:
+        for rec in agents_solve_log(ctx):
+            f.write(json.dumps({"kind": "dal", **rec}) + "\n")
+        for rec in agents_solve_outer_log(ctx):
+            f.write(json.dumps({"kind": "outer", **rec}) + "\n")
+        if info is not None:
+            f.write(json.dumps({"kind": "info", **info.as_dict()}) + "\n")
 
 
 def agents_objective_noalloc(height, width, channels, alpha, rho, tv_mode, c, c0, v, mu,

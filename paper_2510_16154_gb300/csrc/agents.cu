@@ -18,6 +18,7 @@
 #include <new>
 #include <string>
 #include <vector>
+#include <nvtx3/nvToolsExt.h>
 
 using namespace agents;
 
@@ -81,6 +82,12 @@ int fail(agents_ctx* ctx, int code, const char* fmt, ...) {
     int st_ = (expr);          \
     if (st_ != AGENTS_OK) return st_; \
   } while (0)
+
+// NVTX range over a scope (named in profiler timelines; no cost without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 template <class T>
 int dalloc(agents_ctx* ctx, T** out, size_t count) {
@@ -158,6 +165,7 @@ const float* full_state(agents_ctx* ctx, int n) {
 // Forward sweep under the device control d_eps; c^T goes to dst_T.  With store, the
 // states the adjoint needs are kept (all of them, or every k-th).
 int forward_sweep(agents_ctx* ctx, const double* d_eps, float* dst_T, bool store) {
+  NvtxRange nr("forward_sweep");
   const int T = ctx->T;
   const float* cur = ctx->c0;
   int wi = 0;
@@ -201,6 +209,7 @@ int fetch_scalar(agents_ctx* ctx, int slot, double* out) {
 // Reverse sweep from lambda^T held in ctx->lam[0]; D^n (times 1/(2M)) into ctx->d_D.
 // Returns the final lambda^0 buffer in *lam_out.
 int adjoint_sweep_from(agents_ctx* ctx, const double* d_eps, float** lam_out) {
+  NvtxRange nr("adjoint_sweep");
   const int T = ctx->T;
   int li = 0;
   const size_t pstride = (size_t)ctx->nb_adj * 2;
@@ -307,6 +316,7 @@ void ensure_reuse_buffers(agents_ctx* ctx) {
 
 // Full-store forward sweep into a given trajectory buffer and final state.
 int forward_sweep_into(agents_ctx* ctx, const double* d_eps, float* traj, float* dst_T) {
+  NvtxRange nr("trial_sweep");
   const int T = ctx->T;
   const float* cur = ctx->c0;
   for (int n = 0; n < T; ++n) {
@@ -365,6 +375,7 @@ int read_control(agents_ctx* ctx, const double* eps, std::vector<double>& host) 
 int dal_iteration(agents_ctx* ctx, const agents_solve_opts& o, const float* v, const float* mu,
                   int outer, double& sigma, agents_solve_info& inf, std::vector<double>& Dh,
                   std::vector<double>& eps_h, bool& ended) {
+  NvtxRange nr("dal_iteration");
   const int T = ctx->T;
   const double dt = ctx->p.dt;
   const double lo[2] = {ctx->p.eps_lo[0], ctx->p.eps_lo[1]};
@@ -763,6 +774,17 @@ int agents_solve_log(const agents_ctx* ctx, agents_iter_record* out, int32_t cap
   return AGENTS_OK;
 }
 
+int agents_solve_outer_log(const agents_ctx* ctx, agents_outer_record* out, int32_t capacity,
+                           int32_t* count) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  if (count) *count = (int32_t)ctx->outer_log.size();
+  if (out && capacity > 0) {
+    const size_t n = std::min((size_t)capacity, ctx->outer_log.size());
+    std::memcpy(out, ctx->outer_log.data(), n * sizeof(agents_outer_record));
+  }
+  return AGENTS_OK;
+}
+
 int agents_labels(agents_ctx* ctx, const float* c_dev, float threshold, int32_t* labels_out,
                   int32_t* count_out) {
   if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
@@ -844,6 +866,8 @@ int solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float*
   std::vector<double> eps_h;
   TRY(read_control(ctx, eps_io, eps_h));
   ctx->log.clear();
+  ctx->outer_log.clear();
+  NvtxRange nr("solve");
   CK(cudaMemcpyAsync(ctx->d_eps, eps_h.data(), eps_h.size() * sizeof(double),
                      cudaMemcpyHostToDevice, ctx->stream));
   TRY(to_device(ctx, ctx->s_mu, mu_io, ctx->nv * sizeof(float)));
@@ -872,6 +896,7 @@ int solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float*
   std::vector<double> Dh(2 * (size_t)T);
 
   for (int j = 1; j <= o.k_out && status == AGENTS_OK; ++j) {
+    const int inner0 = inf.inner_done;
     // ---- eps-step: k_in iterations of Algorithm 1 on L~(c(T; eps), v, mu)
     for (int it = 0; it < o.k_in; ++it) {
       bool ended = false;
@@ -901,6 +926,8 @@ int solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float*
     inf.final_res = std::max(st[3], dL);
     inf.final_obj = L_new;
     inf.final_gap = st[2];
+    ctx->outer_log.push_back(agents_outer_record{j, inf.inner_done - inner0, L_new, st[4], st[0],
+                                                 st[1], st[2], st[3], inf.final_res, sigma});
     L_prev = L_new;
     if (o.tol > 0.0 && inf.final_res < o.tol) break;
   }

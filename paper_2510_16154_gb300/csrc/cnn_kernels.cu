@@ -318,16 +318,32 @@ __global__ void split_reduce_kernel(const float* __restrict__ part, int splits, 
 }
 
 // Column sums of a [P][C] matrix: per-block partials over pixel ranges, then a fixed-order
-// pass over the blocks.
+// pass over the blocks.  A block's 256 threads form (lanes = 256 / C) rows of C columns
+// (C <= 256; wider matrices loop over column groups): lane l sums pixels p0 + l,
+// p0 + l + lanes, ... of its column, and the lanes are added in order in shared memory.
 constexpr int kColBlocks = 128;
-__global__ void colsum_partial_kernel(const float* __restrict__ a, int P, int C,
-                                      float* __restrict__ part) {
+constexpr int kColThreads = 256;
+__global__ void __launch_bounds__(kColThreads)
+colsum_partial_kernel(const float* __restrict__ a, int P, int C, float* __restrict__ part) {
+  __shared__ float red[kColThreads];
   const int per = (P + gridDim.x - 1) / gridDim.x;
   const int p0 = blockIdx.x * per, p1 = min(P, p0 + per);
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+  const int cw = C < kColThreads ? C : kColThreads;     // columns per group
+  const int lanes = kColThreads / cw;
+  const int c_in = threadIdx.x % cw, lane = threadIdx.x / cw;
+  for (int c0 = 0; c0 < C; c0 += cw) {
+    const int c = c0 + c_in;
     float s = 0.0f;
-    for (int p = p0; p < p1; ++p) s += a[(size_t)p * C + c];
-    part[(size_t)blockIdx.x * C + c] = s;
+    if (lane < lanes && c < C)
+      for (int p = p0 + lane; p < p1; p += lanes) s += a[(size_t)p * C + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if (lane == 0 && c < C) {
+      float t = 0.0f;
+      for (int l = 0; l < lanes; ++l) t += red[l * cw + c_in];
+      part[(size_t)blockIdx.x * C + c] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -413,7 +429,7 @@ cudaError_t conv_backward_weight(const float* x, const float* dy, float* dw, flo
   split_reduce_kernel<<<grid_1d(n), 256, 0, s>>>(ws, used, n, dw);
   if (db) {
     float* part = ws + (size_t)weight_splits(g.K) * n;
-    colsum_partial_kernel<<<kColBlocks, 256, 0, s>>>(dy, g.K, Cout, part);
+    colsum_partial_kernel<<<kColBlocks, kColThreads, 0, s>>>(dy, g.K, Cout, part);
     colsum_final_kernel<<<(Cout + 255) / 256, 256, 0, s>>>(part, kColBlocks, Cout, db);
   }
   return cudaGetLastError();

@@ -67,6 +67,7 @@ struct agents_ctx {
 
   int64_t launches = 0;           // kernels launched by this context (for accounting)
   std::vector<agents_iter_record> log;  // per-DAL-iteration records of the last solve()
+  std::vector<agents_outer_record> outer_log;  // per-multiplier-step records
   std::vector<void*> allocs;
 };
 

@@ -51,6 +51,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(lib.agents_solve_opts) == 3 * 4 + 4 + 4 * 8
     assert ctypes.sizeof(lib.agents_solve_info) == 5 * 4 + 4 + 3 * 8 + 4 * 8 + 8
     assert ctypes.sizeof(lib.agents_iter_record) == 4 * 4 + 4 * 8
+    assert ctypes.sizeof(lib.agents_outer_record) == 2 * 4 + 8 * 8
 
 
 def test_paper_defaults(cdll):

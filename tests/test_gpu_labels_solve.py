@@ -279,3 +279,28 @@ def test_trajectory_reuse_changes_nothing():
     # mode 0 skips the recomputations; mode 3 also recomputes checkpoint segments
     assert i0.forward_steps < i1.forward_steps
     assert j0.forward_steps < j1.forward_steps
+
+
+def test_solve_logs(tmp_path):
+    """Per-multiplier-step records agree with solve_info and the DAL records."""
+    ensure_lib()
+    img = f32(make_image(ImageSpec(30, 34, 3, regions=4, sigma=0.05), 8))
+    p, _ = params(30, 34, 3, 2, 6)
+    o = lib.agents_default_solve_opts()
+    o.k_out, o.k_in = 4, 5
+    eps = np.full((6, 2), 57.0)
+    mu = np.zeros((30, 34, 2, 3), dtype=np.float32)
+    with lib.Context(p, dev(img, np.float32)) as ctx:
+        info = lib.solve(ctx.handle, o, eps, mu)
+        outer = lib.agents_solve_outer_log(ctx.handle)
+        dal = lib.agents_solve_log(ctx.handle)
+        path = tmp_path / "log.jsonl"
+        lib.write_solve_log_jsonl(ctx.handle, str(path), info)
+    assert [r["outer"] for r in outer] == list(range(1, info.outer_done + 1))
+    assert sum(r["inner_done"] for r in outer) == info.inner_done == len(dal)
+    last = outer[-1]
+    assert last["L"] == info.final_obj and last["res"] == info.final_res
+    assert last["gap"] == info.final_gap and last["sigma"] == info.final_sigma
+    assert all(r["r"] >= 0 and r["K"] > 0 and np.isfinite(r["s"]) for r in outer)
+    lines = path.read_text().splitlines()
+    assert len(lines) == len(dal) + len(outer) + 1
