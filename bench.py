@@ -473,6 +473,26 @@ def warmstart_workload(torch, lib, dev, count: int, size: int, reps: int):
             "cold": out["cold"], "warm": out["warm"]}
 
 
+# ---------------------------------------------------------------- replicas over ranks
+
+def rank_seed(rank: int) -> int:
+    """Seed of the image a rank solves: every GPU its own independent problem."""
+    return SEED + rank
+
+
+def reduce_over_ranks(torch, dist, elapsed: float, pixel_steps: float, device):
+    """Whole-job timing of independent replicas: the slowest rank's time and the pixel-
+    steps of all ranks (dist = None for one process).  device: where the collective's
+    tensors live (a CUDA device under NCCL, the CPU under gloo)."""
+    if dist is None:
+        return elapsed, float(pixel_steps)
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([float(pixel_steps)], dtype=torch.float64, device=device)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(s.item())
+
+
 # ---------------------------------------------------------------- CPU oracle leg
 
 ORACLE_ROWS = 256
@@ -619,7 +639,7 @@ def main():
                               **res}), flush=True)
         return 0
 
-    img = make_image(THROUGHPUT_1024_RGB, SEED + rank).astype(np.float32)
+    img = make_image(THROUGHPUT_1024_RGB, rank_seed(rank)).astype(np.float32)
     p = lib.agents_default_params(H, W, C, R, T)
     ctx = lib.Context(p, torch.from_numpy(img).to(dev), stream)
     eps = torch.full((T, 2), 57.0, dtype=torch.float64, device=dev)
@@ -670,15 +690,8 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     elapsed = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-    t_max = elapsed
-    total_ps = pixel_steps
-    if world > 1:
-        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        s = torch.tensor([float(pixel_steps)], dtype=torch.float64, device=dev)
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        total_ps = float(s.item())
+    t_max, total_ps = reduce_over_ranks(torch, dist if world > 1 else None, elapsed,
+                                        pixel_steps, dev)
     value = total_ps / t_max / 1e6
 
     # ---- roofline of the dominant kernel (the forward Euler step), timed live: one

@@ -1,0 +1,55 @@
+"""The N > 1 path of bench.py on CPU: two gloo ranks (replicas only: every rank solves
+its own image, the only collective is the whole-job timing).  The slowest rank's time
+and the sum of all ranks' pixel-steps give the aggregate; ranks get distinct images; the
+reference arm runs on rank 0 only."""
+import os
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        t, ps = bench.reduce_over_ranks(torch, dist, elapsed=1.5 + rank, pixel_steps=1000 * (rank + 1),
+                                        device="cpu")
+        out[rank] = (t, ps, bench.rank_seed(rank))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_aggregate_like_the_bench():
+    port = 29500 + os.getpid() % 1000
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_worker, args=(2, port, out), nprocs=2, start_method="spawn")
+        res = dict(out)
+    assert res[0][:2] == res[1][:2] == (2.5, 3000.0)       # max time, summed work
+    assert res[0][2] != res[1][2]                            # independent images
+
+
+def test_single_process_needs_no_collective():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_over_ranks(torch, None, 2.0, 7, "cpu") == (2.0, 7.0)
+
+
+def test_reference_arm_is_rank0_only(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class A:
+        warmup, steps = 1, 1
+    called = []
+    monkeypatch.setattr(bench, "oracle_sample", lambda: called.append(1) or (1, 1.0))
+    assert bench.run_reference(A, rank=1, world=2) == 0
+    assert called == [] and capsys.readouterr().out == ""
