@@ -28,6 +28,13 @@ struct Wide {
   static constexpr size_t smem(int nf) { return (size_t)(nf * C + 1) * PLANE * sizeof(float); }
 };
 
+// 4-byte asynchronous copy global -> shared: a thread issues all its copies of a tile
+// without waiting on each load, and waits once (wide_load_wait).
+__device__ __forceinline__ void wide_cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 // Stage NF fields (NHWC, C channels) of the tile at (x0, y0) plus its halo.  Cells outside
 // the image hold 0 and, when the halo leaves the image, the validity plane marks them 0.
 template <class T, int R, int C, int NF>
@@ -48,8 +55,8 @@ __device__ __forceinline__ bool wide_load(float* __restrict__ sm, const float* _
     float* row = sm + yy * T::SW + xa;
     for (int f = tid; f < nval; f += T::NT) {
       const int px = f / C, ch = f - px * C;
-      row[ch * T::PLANE + px] = __ldg(f0 + base + f);
-      if constexpr (NF == 2) row[(C + ch) * T::PLANE + px] = __ldg(f1 + base + f);
+      wide_cp_async4(row + ch * T::PLANE + px, f0 + base + f);
+      if constexpr (NF == 2) wide_cp_async4(row + (C + ch) * T::PLANE + px, f1 + base + f);
     }
     for (int xx = tid; xx < T::SW; xx += T::NT) {
       const bool ok = rowok && xx >= xa && xx < xb;
@@ -60,6 +67,7 @@ __device__ __forceinline__ bool wide_load(float* __restrict__ sm, const float* _
       if (border) mask[yy * T::SW + xx] = ok ? 1.0f : 0.0f;
     }
   }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   return border;
 }
@@ -106,14 +114,14 @@ __device__ __forceinline__ void wide_forward_body(float* __restrict__ sm, float*
     for (int dx = -R; dx <= R; ++dx) {
       const int e = cen + dy * T::SW + dx;
       float d[C];
-      float s2a = 0.0f, s2b = 0.0f;
+      float s2p[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // four independent chains
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) {
         d[ch] = sm[ch * T::PLANE + e] - ci[ch];
-        if (ch & 1) s2b = fmaf(d[ch], d[ch], s2b);
-        else s2a = fmaf(d[ch], d[ch], s2a);
+        s2p[ch & 3] = fmaf(d[ch], d[ch], s2p[ch & 3]);
       }
-      const float t = fmaxf(fmaf(-kc, s2a + s2b, fmaf(-kx, (float)(dx * dx), sy)), 0.0f);
+      const float s2 = (s2p[0] + s2p[1]) + (s2p[2] + s2p[3]);
+      const float t = fmaxf(fmaf(-kc, s2, fmaf(-kx, (float)(dx * dx), sy)), 0.0f);
       const float t2 = t * t;
       float ph = (t2 * t2) * fmaf(-4.0f, t, 5.0f);
       if constexpr (BORDER) ph *= mask[e];
@@ -154,15 +162,20 @@ __device__ __forceinline__ void wide_adjoint_body(float* __restrict__ sm, float*
     for (int dx = -R; dx <= R; ++dx) {
       const int e = cen + dy * T::SW + dx;
       float d[C], dl[C];
-      float s2 = 0.0f, proj = 0.0f, lkd = 0.0f;
+      // each channel sum in four independent chains (latency of the FMA chains)
+      float s2p[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      float lp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) {
         d[ch] = sc[ch * T::PLANE + e] - ck[ch];
         dl[ch] = sl[ch * T::PLANE + e] - lk[ch];
-        s2 = fmaf(d[ch], d[ch], s2);
-        proj = fmaf(d[ch], dl[ch], proj);
-        lkd = fmaf(lk[ch], d[ch], lkd);
+        s2p[ch & 3] = fmaf(d[ch], d[ch], s2p[ch & 3]);
+        pp[ch & 3] = fmaf(d[ch], dl[ch], pp[ch & 3]);
+        lp[ch & 3] = fmaf(lk[ch], d[ch], lp[ch & 3]);
       }
+      const float s2 = (s2p[0] + s2p[1]) + (s2p[2] + s2p[3]);
+      const float proj = (pp[0] + pp[1]) + (pp[2] + pp[3]);
+      const float lkd = (lp[0] + lp[1]) + (lp[2] + lp[3]);
       const float t = fmaxf(fmaf(-kc, s2, fmaf(-kx, (float)(dx * dx), sy)), 0.0f);
       const float t2 = t * t, t3 = t2 * t;
       float ph = (t2 * t2) * fmaf(-4.0f, t, 5.0f);
