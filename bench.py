@@ -429,7 +429,7 @@ def warmstart_workload(torch, lib, dev, count: int, size: int, reps: int):
     RGB images (Voronoi K ~ U{4..32}, ramp 0.1, sigma ~ U[0.02, 0.15]) of size^2, R = 5,
     T = 20, k_in = 10, at most 40 multiplier steps, solved as one batched solve (CUDA
     graphs, autotuned tiles) from the cold start (mu = 0, eps = 57) and from the
-    committed network's mu.  Device time per solve (CUDA events on the batch's stream
+    committed network's mu and eps.  Device time per solve (CUDA events on the batch's stream
     order: synchronised around each call), network inference included in the warm arm."""
     from paper_2510_16154_gb300.train_warmstart import make_images, R as R_WS, T as T_WS
     from paper_2510_16154_gb300.warmstart import WarmStartNet, WEIGHTS_DIR
@@ -448,8 +448,9 @@ def warmstart_workload(torch, lib, dev, count: int, size: int, reps: int):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             if mode == "warm":
-                mu_p, _ = net.predict(imgs)
+                mu_p, eps_p = net.predict(imgs)
                 mus = [mu_p[i].reshape(size, size, 2, 3).contiguous() for i in range(count)]
+                eps = [eps_p[i].contiguous() for i in range(count)]
             infos = lib.agents_solve_batch([c.handle for c in ctxs], o, eps, mus, None,
                                            autotune=True, use_graph=True)
             torch.cuda.synchronize()

@@ -2,7 +2,7 @@
  *
  * The paper starts every solve of Algorithm 2 from the dual field mu(0) = 0 and the control
  * eps(0) = 57 (Section 5).  This network predicts both from the image, so that the solve
- * starts closer to its fixed point; the solve itself is unchanged and remains the judge of
+ * starts closer to its fixed point; the solve itself is unchanged and still decides
  * the result (the paper has no counterpart of the network).
  *
  * Architecture (levels L, base width B, widths B 2^(l-1) for l = 1..L):
@@ -82,7 +82,7 @@ typedef struct ws_net_config {
   int32_t in_ch;    /* image channels */
   int32_t out_ch;   /* mu channels (2 C) */
   int32_t base;     /* width of level 1 */
-  int32_t levels;   /* >= 1; H and W are padded to multiples of 2^(levels-1) */
+  int32_t levels;   /* 2..8; H and W are padded to multiples of 2^(levels-1) */
   int32_t nsteps;   /* T: the control head has 2T outputs */
   float eps_lo[2];  /* box E for the predicted control */
   float eps_hi[2];

@@ -5,7 +5,7 @@ Marshalling only: the network's convolutions, pooling, heads, loss gradient and 
 updates all run in ``libagents.so`` (BF16 tensor-core convolutions with float32
 accumulation).  PyTorch holds the device buffers.
 
-The solve stays the judge of the answer: ``warm_solve`` starts solve() from the
+The solve still decides the answer: ``warm_solve`` starts solve() from the
 prediction and, if that solve diverges or ends without reaching the tolerance, runs the
 plain cold-started solve instead (the fallback).
 """
@@ -202,9 +202,9 @@ class WarmStartNet:
         return history
 
 
-def warm_solve(ctx_handle, net: WarmStartNet, img: torch.Tensor, opts, use_eps: bool = False,
+def warm_solve(ctx_handle, net: WarmStartNet, img: torch.Tensor, opts, use_eps: bool = True,
                c_out=None, fallback_on_miss: bool = False):
-    """solve() started from the network's mu(0) (and its eps(0) with use_eps); falls back
+    """solve() started from the network's mu(0) and eps(0) (mu only without use_eps); falls back
     to the cold start (mu = 0, eps = 57) when the warm solve diverges (AGENTS_EDIVERGED),
     and with fallback_on_miss also when it ends without reaching opts.tol.
     Returns (info, eps, mu, used_fallback)."""
