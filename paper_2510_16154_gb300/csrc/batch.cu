@@ -319,9 +319,10 @@ int size_bucket(long long pixels) {
 }
 
 std::vector<BatchJob> sweep_jobs(const std::vector<agents_ctx*>& ctxs, const std::vector<int>& ids,
-                                 int shape, bool tiled) {
+                                 int shape, bool tiled, int R, int C) {
   std::vector<BatchJob> jobs;
-  const int tw = tiled ? batch_tile_w(shape) : 32, th = tiled ? batch_tile_h(shape) : 4;
+  const int tw = tiled ? batch_tile_w(shape) : 32;
+  const int th = tiled ? batch_tile_h(shape) : untiled_tile_h(R, C);
   for (int i : ids) {
     const int W = ctxs[i]->p.width, H = ctxs[i]->p.height;
     for (int ty = 0; ty < (H + th - 1) / th; ++ty)
@@ -463,7 +464,8 @@ extern "C" int agents_solve_batch(int32_t n, agents_ctx* const* ctx_list,
   auto fill_imgs = [&](const std::vector<SweepClass>& cls) {
     for (const auto& sc : cls) {
       const bool tiled = batch_tiled(sc.R, sc.C);
-      const int tw = tiled ? batch_tile_w(sc.shape) : 32, th = tiled ? batch_tile_h(sc.shape) : 4;
+      const int tw = tiled ? batch_tile_w(sc.shape) : 32;
+      const int th = tiled ? batch_tile_h(sc.shape) : untiled_tile_h(sc.R, sc.C);
       for (int i : by_rc[{sc.R, sc.C}]) {
         agents_ctx* c = ctxs[i];
         BatchSweepImg& im = h_imgs[i];
@@ -518,15 +520,22 @@ extern "C" int agents_solve_batch(int32_t n, agents_ctx* const* ctx_list,
     }
     float best_ms = 1e30f;
     int best_shape = 0;
-    cudaEvent_t e0, e1;
-    BCK(cudaEventCreate(&e0));
-    BCK(cudaEventCreate(&e1));
+    struct Events {  // destroyed on every return path
+      cudaEvent_t a = nullptr, b = nullptr;
+      ~Events() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+      }
+    } ev;
+    BCK(cudaEventCreate(&ev.a));
+    BCK(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     for (int shape = 0; shape < kNumShapes; ++shape) {
       sc.shape = shape;
       fill_imgs(sweeps);
       BCK(cudaMemcpyAsync(d_imgs.p, h_imgs.data(), n * sizeof(BatchSweepImg),
                           cudaMemcpyHostToDevice, s));
-      std::vector<BatchJob> jobs = sweep_jobs(ctxs, ids, shape, true);
+      std::vector<BatchJob> jobs = sweep_jobs(ctxs, ids, shape, true, sc.R, sc.C);
       DevBuf<BatchJob> dj;
       BCK(dj.alloc(jobs.size()));
       BCK(cudaMemcpyAsync(dj.p, jobs.data(), jobs.size() * sizeof(BatchJob), cudaMemcpyHostToDevice, s));
@@ -542,8 +551,6 @@ extern "C" int agents_solve_batch(int32_t n, agents_ctx* const* ctx_list,
       BCK(cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best_ms) { best_ms = ms; best_shape = shape; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     sc.shape = best_shape;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tuned[key] = best_shape;
@@ -551,7 +558,8 @@ extern "C" int agents_solve_batch(int32_t n, agents_ctx* const* ctx_list,
   fill_imgs(sweeps);
   BCK(cudaMemcpyAsync(d_imgs.p, h_imgs.data(), n * sizeof(BatchSweepImg), cudaMemcpyHostToDevice, s));
   for (auto& sc : sweeps) {
-    sc.jobs = sweep_jobs(ctxs, by_rc[{sc.R, sc.C}], sc.shape, batch_tiled(sc.R, sc.C));
+    sc.jobs = sweep_jobs(ctxs, by_rc[{sc.R, sc.C}], sc.shape, batch_tiled(sc.R, sc.C), sc.R,
+                         sc.C);
     BCK(sc.d_jobs.alloc(sc.jobs.size()));
     BCK(cudaMemcpyAsync(sc.d_jobs.p, sc.jobs.data(), sc.jobs.size() * sizeof(BatchJob),
                         cudaMemcpyHostToDevice, s));

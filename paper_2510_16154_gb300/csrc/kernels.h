@@ -49,6 +49,9 @@ enum { kSweepStore = 0, kSweepTrial = 1 };
 constexpr int kNumShapes = 3;
 int batch_tile_w(int shape);
 int batch_tile_h(int shape);
+// Tile height of the kernels without a tiled (R, C) instantiation (tile width 32): the
+// wide-channel tiles for C = 31, the generic kernels' 4 rows otherwise.
+int untiled_tile_h(int R, int C);
 bool batch_tiled(int R, int C);
 // Step n of the forward sweep of `kind` for every job whose image is active.
 cudaError_t launch_forward_batch(const BatchSweepImg* imgs, const BatchJob* jobs, int njobs,

@@ -77,7 +77,8 @@ static int adjoint_blocks_tiled(const SweepGeom& g) {
 
 int adjoint_num_blocks(const SweepGeom& g) {
 #define AGENTS_NB(R, C) adjoint_blocks_tiled<R, C>(g)
-  AGENTS_DISPATCH_RC(g.R, g.C, AGENTS_NB, ceil_div(g.W, kGenBX) * ceil_div(g.H, kGenBY));
+  AGENTS_DISPATCH_RC(g.R, g.C, AGENTS_NB,
+                     ceil_div(g.W, kGenBX) * ceil_div(g.H, untiled_tile_h(g.R, g.C)));
 #undef AGENTS_NB
 }
 

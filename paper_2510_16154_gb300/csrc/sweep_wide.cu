@@ -24,7 +24,7 @@ cudaError_t fwd(const float* c_in, float* c_out, const double* eps_n, const Swee
   cudaError_t e = opt_in_smem(kern, smem, attr);
   if (e != cudaSuccess) return e;
   dim3 grid(ceil_div(g.W, T::TW), ceil_div(g.H, T::TH));
-  kern<<<grid, dim3(kWideBX, kWideBY), smem, s>>>(c_in, c_out, eps_n, g);
+  kern<<<grid, dim3(kWideBX, T::TH), smem, s>>>(c_in, c_out, eps_n, g);
   return cudaGetLastError();
 }
 
@@ -38,7 +38,7 @@ cudaError_t adj(const float* c_n, const float* lam_next, float* lam_out, const d
   cudaError_t e = opt_in_smem(kern, smem, attr);
   if (e != cudaSuccess) return e;
   dim3 grid(ceil_div(g.W, T::TW), ceil_div(g.H, T::TH));
-  kern<<<grid, dim3(kWideBX, kWideBY), smem, s>>>(c_n, lam_next, lam_out, eps_n, partial, g);
+  kern<<<grid, dim3(kWideBX, T::TH), smem, s>>>(c_n, lam_next, lam_out, eps_n, partial, g);
   return cudaGetLastError();
 }
 
@@ -54,7 +54,7 @@ cudaError_t fwd_batch(const BatchSweepImg* imgs, const BatchJob* jobs, int njobs
   if (e != cudaSuccess) return e;
   grid = grid < njobs ? grid : njobs;
   if (grid <= 0) return cudaSuccess;
-  kern<<<grid, dim3(kWideBX, kWideBY), smem, s>>>(imgs, jobs, njobs, active, n, kind);
+  kern<<<grid, dim3(kWideBX, T::TH), smem, s>>>(imgs, jobs, njobs, active, n, kind);
   return cudaGetLastError();
 }
 
@@ -70,11 +70,13 @@ cudaError_t adj_batch(const BatchSweepImg* imgs, const BatchJob* jobs, int njobs
   if (e != cudaSuccess) return e;
   grid = grid < njobs ? grid : njobs;
   if (grid <= 0) return cudaSuccess;
-  kern<<<grid, dim3(kWideBX, kWideBY), smem, s>>>(imgs, jobs, njobs, active, n);
+  kern<<<grid, dim3(kWideBX, T::TH), smem, s>>>(imgs, jobs, njobs, active, n);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+int untiled_tile_h(int R, int C) { return wide_shape(R, C) ? wide_tile_h(R) : kGenBY; }
 
 #define AGENTS_WIDE_R(R_, CALL)                                   \
   switch (R_) {                                                   \

@@ -6,7 +6,7 @@
 // shared-memory and FP32 rates.  Tile loads read each tile row as one flat, coalesced
 // NHWC segment; the results are staged back through shared memory and stored the same
 // way.  The 32 x 4 tile is the generic kernels' tile, so per-tile partial sums and batch
-// job lists are laid out alike.
+// job lists are laid out alike (32 x 8 tiles for R <= 6: see wide_by).
 #pragma once
 
 #include "sweep.cuh"
@@ -20,9 +20,16 @@ constexpr int kWideC = 31;          // the channel count with a wide instantiati
 // would need 242 KB of shared memory (227 KB per block at most).
 inline bool wide_shape(int R, int C) { return R >= 1 && R <= 7 && C == kWideC; }
 
+// Tile height: 8 rows where the adjoint's tile of both fields still fits (R <= 6: 190 KB
+// at R = 5, 222 KB at R = 6), else 4.  Taller tiles load fewer halo cells per output
+// pixel and run twice the warps per block.
+template <int R>
+constexpr int wide_by() { return R <= 6 ? 8 : kWideBY; }
+inline int wide_tile_h(int R) { return R <= 6 ? 8 : kWideBY; }
+
 template <int R, int C>
 struct Wide {
-  static constexpr int TW = kWideBX, TH = kWideBY, NT = kWideBX * kWideBY;
+  static constexpr int TW = kWideBX, TH = wide_by<R>(), NT = kWideBX * wide_by<R>();
   static constexpr int SW = TW + 2 * R, SH = TH + 2 * R, PLANE = SW * SH;
   // planes: NF fields x C channels, then the validity plane
   static constexpr size_t smem(int nf) { return (size_t)(nf * C + 1) * PLANE * sizeof(float); }
@@ -206,7 +213,7 @@ __device__ __forceinline__ void wide_adjoint_body(float* __restrict__ sm, float*
 }
 
 template <int R, int C>
-__global__ void __launch_bounds__(kWideBX * kWideBY)
+__global__ void __launch_bounds__(kWideBX * wide_by<R>())
 wide_forward_kernel(const float* __restrict__ c, float* __restrict__ out,
                     const double* __restrict__ eps_n, SweepGeom g) {
   using T = Wide<R, C>;
@@ -221,7 +228,7 @@ wide_forward_kernel(const float* __restrict__ c, float* __restrict__ out,
 }
 
 template <int R, int C>
-__global__ void __launch_bounds__(kWideBX * kWideBY)
+__global__ void __launch_bounds__(kWideBX * wide_by<R>())
 wide_adjoint_kernel(const float* __restrict__ c, const float* __restrict__ lam,
                     float* __restrict__ out, const double* __restrict__ eps_n,
                     double* __restrict__ partial, SweepGeom g) {
@@ -239,7 +246,7 @@ wide_adjoint_kernel(const float* __restrict__ c, const float* __restrict__ lam,
 
 // Batched (persistent) versions: step n of every (image, tile) job of the batch.
 template <int R, int C>
-__global__ void __launch_bounds__(kWideBX * kWideBY)
+__global__ void __launch_bounds__(kWideBX * wide_by<R>())
 wide_forward_batch_kernel(const BatchSweepImg* __restrict__ imgs, const BatchJob* __restrict__ jobs,
                           int njobs, const int* __restrict__ active, int n, int kind) {
   using T = Wide<R, C>;
@@ -274,7 +281,7 @@ wide_forward_batch_kernel(const BatchSweepImg* __restrict__ imgs, const BatchJob
 }
 
 template <int R, int C>
-__global__ void __launch_bounds__(kWideBX * kWideBY)
+__global__ void __launch_bounds__(kWideBX * wide_by<R>())
 wide_adjoint_batch_kernel(const BatchSweepImg* __restrict__ imgs, const BatchJob* __restrict__ jobs,
                           int njobs, const int* __restrict__ active, int n) {
   using T = Wide<R, C>;
