@@ -9,7 +9,8 @@
 // The operands are gathered from NHWC float32 tensors (zero outside the image), rounded to
 // bfloat16 (nearest even) and staged in shared memory; the next K-chunk is fetched into
 // registers while the current one is multiplied.  Backward-weight splits the pixel sum
-// over blocks and adds the partial sums in a fixed order.
+// over blocks and adds the partial sums in a fixed order; its operands arrive pixel by
+// pixel, so its tiles are stored k-major and transposed by ldmatrix.trans.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -21,6 +22,11 @@ namespace ws {
 
 constexpr int BM = 128, BN = 64, BK = 32, NT = 256;
 constexpr int SK = BK + 8;  // shared-memory row stride (bf16): conflict-free fragment loads
+// Backward-weight keeps its tiles k-major (k rows, m or n contiguous: the operands arrive
+// pixel by pixel) and builds the fragments with ldmatrix.trans; the row strides keep the
+// eight 16-byte rows of every 8x8 matrix in distinct banks.
+constexpr int SAT = BM + 8, SBT = BN + 8;
+static_assert(BK * SAT <= BM * SK && BK * SBT <= BN * SK, "k-major tiles reuse the buffers");
 
 struct GemmArgs {
   int mode;
@@ -43,6 +49,15 @@ struct GemmArgs {
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Four 8x8 bf16 matrices from shared memory, transposed (lane l gives the row address of
+// matrix l / 8, row l % 8; each row 16 contiguous bytes).
+__device__ __forceinline__ void ldmatrix_x4_trans(uint32_t (&r)[4], const __nv_bfloat16* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
 }
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
@@ -235,13 +250,15 @@ __global__ void __launch_bounds__(NT) igemm_kernel(GemmArgs g) {
       *reinterpret_cast<uint4*>(&As[a_row * SK + a_k]) = make_uint4(ra[0][0], ra[0][1], ra[0][2], ra[0][3]);
       *reinterpret_cast<uint4*>(&As[a_row * SK + a_k + 8]) = make_uint4(ra[1][0], ra[1][1], ra[1][2], ra[1][3]);
       *reinterpret_cast<uint4*>(&Bs[b_row * SK + b_k]) = make_uint4(rb[0], rb[1], rb[2], rb[3]);
-    } else {
+    } else {  // k-major: 8 consecutive m (or n) of one pixel k as one 16-byte store
 #pragma unroll
       for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) As[(a_row + 8 * h + j) * SK + a_k] = __float2bfloat16_rn(fa[h][j]);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) Bs[(b_row + j) * SK + b_k] = __float2bfloat16_rn(fb[j]);
+        *reinterpret_cast<uint4*>(&As[a_k * SAT + a_row + 8 * h]) =
+            make_uint4(pack_bf16(fa[h][0], fa[h][1]), pack_bf16(fa[h][2], fa[h][3]),
+                       pack_bf16(fa[h][4], fa[h][5]), pack_bf16(fa[h][6], fa[h][7]));
+      *reinterpret_cast<uint4*>(&Bs[b_k * SBT + b_row]) =
+          make_uint4(pack_bf16(fb[0], fb[1]), pack_bf16(fb[2], fb[3]), pack_bf16(fb[4], fb[5]),
+                     pack_bf16(fb[6], fb[7]));
     }
   };
 
@@ -262,21 +279,42 @@ __global__ void __launch_bounds__(NT) igemm_kernel(GemmArgs g) {
 #pragma unroll
     for (int ks = 0; ks < BK; ks += 16) {
       uint32_t a[2][4];
+      if constexpr (MODE == 2) {
+        // matrices (k lo, m lo), (k lo, m hi), (k hi, m lo), (k hi, m hi) = a0..a3
+        const int q = lane >> 3, r = lane & 7;
 #pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r0 = wm + i * 16 + gid, c0 = ks + tig * 2;
-        a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r0 * SK + c0]);
-        a[i][1] = *reinterpret_cast<const uint32_t*>(&As[(r0 + 8) * SK + c0]);
-        a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r0 * SK + c0 + 8]);
-        a[i][3] = *reinterpret_cast<const uint32_t*>(&As[(r0 + 8) * SK + c0 + 8]);
-      }
+        for (int i = 0; i < 2; ++i)
+          ldmatrix_x4_trans(a[i], &As[(ks + ((q & 2) ? 8 : 0) + r) * SAT + wm + i * 16 +
+                                      ((q & 1) ? 8 : 0)]);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n = wn + j * 8 + gid, c0 = ks + tig * 2;
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Bs[n * SK + c0]);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Bs[n * SK + c0 + 8]);
+        for (int jj = 0; jj < 4; jj += 2) {
+          // matrices (k lo, n), (k hi, n), (k lo, n + 8), (k hi, n + 8) = b0, b1 of two blocks
+          uint32_t b[4];
+          ldmatrix_x4_trans(b, &Bs[(ks + ((q & 1) ? 8 : 0) + r) * SBT + wn + jj * 8 +
+                                   ((q & 2) ? 8 : 0)]);
 #pragma unroll
-        for (int i = 0; i < 2; ++i) mma_bf16(acc[i][j], a[i], b0, b1);
+          for (int i = 0; i < 2; ++i) {
+            mma_bf16(acc[i][jj], a[i], b[0], b[1]);
+            mma_bf16(acc[i][jj + 1], a[i], b[2], b[3]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int r0 = wm + i * 16 + gid, c0 = ks + tig * 2;
+          a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r0 * SK + c0]);
+          a[i][1] = *reinterpret_cast<const uint32_t*>(&As[(r0 + 8) * SK + c0]);
+          a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r0 * SK + c0 + 8]);
+          a[i][3] = *reinterpret_cast<const uint32_t*>(&As[(r0 + 8) * SK + c0 + 8]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int n = wn + j * 8 + gid, c0 = ks + tig * 2;
+          const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Bs[n * SK + c0]);
+          const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Bs[n * SK + c0 + 8]);
+#pragma unroll
+          for (int i = 0; i < 2; ++i) mma_bf16(acc[i][j], a[i], b0, b1);
+        }
       }
     }
   }
