@@ -1,12 +1,11 @@
 // Agent sweep kernels for wide channel counts (hyperspectral images, C = 31): one pixel
-// per thread on 32 x 4 pixel tiles, every channel of the tile and its halo staged in
-// channel-planar shared memory (plane ch holds channel ch of the tile), and the channel
-// loop unrolled in registers.  Each interaction reads C floats of the neighbour from
-// shared memory and does about 3C FMAs, so the kernels sit near the balance of the
-// shared-memory and FP32 rates.  Tile loads read each tile row as one flat, coalesced
-// NHWC segment; the results are staged back through shared memory and stored the same
-// way.  The 32 x 4 tile is the generic kernels' tile, so per-tile partial sums and batch
-// job lists are laid out alike (32 x 8 tiles for R <= 6: see wide_by).
+// per thread on 32-pixel-wide tiles, every tile cell (tile pixel or halo pixel) staged in
+// shared memory as one record holding all its channels (and, for the adjoint, the adjoint
+// state after them), then the validity flag, padded to a stride that keeps vector loads of
+// consecutive cells conflict-free.  A neighbour's record is read with 8-byte (forward) or
+// 16-byte (adjoint) loads and the channel loop is unrolled in registers.  Tiles are staged
+// with asynchronous copies (cp.async) from flat, coalesced NHWC row segments; results are
+// staged back through shared memory and stored the same way.  Tile height: see wide_by.
 #pragma once
 
 #include "sweep.cuh"
@@ -20,19 +19,28 @@ constexpr int kWideC = 31;          // the channel count with a wide instantiati
 // would need 242 KB of shared memory (227 KB per block at most).
 inline bool wide_shape(int R, int C) { return R >= 1 && R <= 7 && C == kWideC; }
 
-// Tile height: 8 rows where the adjoint's tile of both fields still fits (R <= 6: 190 KB
-// at R = 5, 222 KB at R = 6), else 4.  Taller tiles load fewer halo cells per output
-// pixel and run twice the warps per block.
+// Tile height: 8 rows where both fields of the adjoint's tile fit (R <= 5: 206 KB of
+// shared memory at R = 5), else 4.  Taller tiles load fewer halo cells per output pixel
+// and run twice the warps per block.
 template <int R>
-constexpr int wide_by() { return R <= 6 ? 8 : kWideBY; }
-inline int wide_tile_h(int R) { return R <= 6 ? 8 : kWideBY; }
+constexpr int wide_by() { return R <= 5 ? 8 : kWideBY; }
+inline int wide_tile_h(int R) { return R <= 5 ? 8 : kWideBY; }
+
+// Record stride (floats) of a cell holding `raw` values: forward records are read with
+// 8-byte loads (stride/2 odd: 16 consecutive cells hit distinct banks), adjoint records
+// with 16-byte loads (stride/4 odd: 8 consecutive cells hit distinct banks).
+constexpr int wide_rec2(int raw) { return ((raw + 1) / 2) % 2 ? ((raw + 1) / 2) * 2 : ((raw + 1) / 2 + 1) * 2; }
+constexpr int wide_rec4(int raw) { return ((raw + 3) / 4) % 2 ? ((raw + 3) / 4) * 4 : ((raw + 3) / 4 + 1) * 4; }
 
 template <int R, int C>
 struct Wide {
   static constexpr int TW = kWideBX, TH = wide_by<R>(), NT = kWideBX * wide_by<R>();
-  static constexpr int SW = TW + 2 * R, SH = TH + 2 * R, PLANE = SW * SH;
-  // planes: NF fields x C channels, then the validity plane
-  static constexpr size_t smem(int nf) { return (size_t)(nf * C + 1) * PLANE * sizeof(float); }
+  static constexpr int SW = TW + 2 * R, SH = TH + 2 * R, CELLS = SW * SH;
+  static constexpr int REC1 = wide_rec2(C + 1);       // forward: C values, flag
+  static constexpr int REC2 = wide_rec4(2 * C + 1);   // adjoint: C values, C adjoints, flag
+  static constexpr size_t smem(int nf) {
+    return (size_t)CELLS * (nf == 1 ? REC1 : REC2) * sizeof(float);
+  }
 };
 
 // 4-byte asynchronous copy global -> shared: a thread issues all its copies of a tile
@@ -42,15 +50,17 @@ __device__ __forceinline__ void wide_cp_async4(float* dst, const float* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 
-// Stage NF fields (NHWC, C channels) of the tile at (x0, y0) plus its halo.  Cells outside
-// the image hold 0 and, when the halo leaves the image, the validity plane marks them 0.
+// Stage NF fields (NHWC, C channels) of the tile at (x0, y0) plus its halo into cell
+// records: values of field f, channel ch at slot f * C + ch, the validity flag at slot
+// NF * C.  Cells outside the image hold 0; the flag is written only when the halo leaves
+// the image (interior tiles never read it).
 template <class T, int R, int C, int NF>
 __device__ __forceinline__ bool wide_load(float* __restrict__ sm, const float* __restrict__ f0,
                                           const float* __restrict__ f1, const SweepGeom& g,
                                           int x0, int y0) {
+  constexpr int REC = NF == 1 ? T::REC1 : T::REC2;
   const bool border = (x0 - R < 0) || (y0 - R < 0) || (x0 + T::TW + R > g.W) ||
                       (y0 + T::TH + R > g.H);
-  float* mask = sm + NF * C * T::PLANE;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int gx0 = x0 - R;
   const int xa = max(0, -gx0), xb = min(T::SW, g.W - gx0);   // valid columns [xa, xb)
@@ -59,19 +69,20 @@ __device__ __forceinline__ bool wide_load(float* __restrict__ sm, const float* _
     const bool rowok = gy >= 0 && gy < g.H;
     const int nval = (rowok && xb > xa) ? (xb - xa) * C : 0;
     const size_t base = rowok ? ((size_t)gy * g.W + (gx0 + xa)) * C : 0;
-    float* row = sm + yy * T::SW + xa;
+    float* row = sm + (size_t)(yy * T::SW + xa) * REC;
     for (int f = tid; f < nval; f += T::NT) {
       const int px = f / C, ch = f - px * C;
-      wide_cp_async4(row + ch * T::PLANE + px, f0 + base + f);
-      if constexpr (NF == 2) wide_cp_async4(row + (C + ch) * T::PLANE + px, f1 + base + f);
+      wide_cp_async4(row + px * REC + ch, f0 + base + f);
+      if constexpr (NF == 2) wide_cp_async4(row + px * REC + C + ch, f1 + base + f);
     }
     for (int xx = tid; xx < T::SW; xx += T::NT) {
       const bool ok = rowok && xx >= xa && xx < xb;
+      float* cell = sm + (size_t)(yy * T::SW + xx) * REC;
       if (!ok) {
 #pragma unroll 4
-        for (int ch = 0; ch < NF * C; ++ch) sm[ch * T::PLANE + yy * T::SW + xx] = 0.0f;
+        for (int k = 0; k < NF * C; ++k) cell[k] = 0.0f;
       }
-      if (border) mask[yy * T::SW + xx] = ok ? 1.0f : 0.0f;
+      if (border) cell[NF * C] = ok ? 1.0f : 0.0f;
     }
   }
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
@@ -106,12 +117,12 @@ template <class T, int R, int C, bool BORDER>
 __device__ __forceinline__ void wide_forward_body(float* __restrict__ sm, float* __restrict__ out,
                                                   const SweepGeom& g, float kx, float ky,
                                                   float kc, int x0, int y0) {
-  const float* mask = sm + C * T::PLANE;
+  constexpr int REC = T::REC1, NV = REC / 2;
   const int cen = (threadIdx.y + R) * T::SW + threadIdx.x + R;
   float ci[C], acc[C];
 #pragma unroll
   for (int ch = 0; ch < C; ++ch) {
-    ci[ch] = sm[ch * T::PLANE + cen];
+    ci[ch] = sm[cen * REC + ch];
     acc[ch] = 0.0f;
   }
 #pragma unroll 1
@@ -120,18 +131,26 @@ __device__ __forceinline__ void wide_forward_body(float* __restrict__ sm, float*
 #pragma unroll 1
     for (int dx = -R; dx <= R; ++dx) {
       const int e = cen + dy * T::SW + dx;
+      const float2* rec = reinterpret_cast<const float2*>(sm + e * REC);
+      float v[2 * NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const float2 t = rec[q];
+        v[2 * q] = t.x;
+        v[2 * q + 1] = t.y;
+      }
       float d[C];
       float s2p[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // four independent chains
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) {
-        d[ch] = sm[ch * T::PLANE + e] - ci[ch];
+        d[ch] = v[ch] - ci[ch];
         s2p[ch & 3] = fmaf(d[ch], d[ch], s2p[ch & 3]);
       }
       const float s2 = (s2p[0] + s2p[1]) + (s2p[2] + s2p[3]);
       const float t = fmaxf(fmaf(-kc, s2, fmaf(-kx, (float)(dx * dx), sy)), 0.0f);
       const float t2 = t * t;
       float ph = (t2 * t2) * fmaf(-4.0f, t, 5.0f);
-      if constexpr (BORDER) ph *= mask[e];
+      if constexpr (BORDER) ph *= v[C];
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) acc[ch] = fmaf(ph, d[ch], acc[ch]);
     }
@@ -148,15 +167,13 @@ __device__ __forceinline__ void wide_adjoint_body(float* __restrict__ sm, float*
                                                   double* __restrict__ partial, const SweepGeom& g,
                                                   float kx, float ky, float kc, float ec, int x0,
                                                   int y0) {
-  const float* sc = sm;
-  const float* sl = sm + C * T::PLANE;
-  const float* mask = sm + 2 * C * T::PLANE;
+  constexpr int REC = T::REC2, NV = REC / 4;
   const int cen = (threadIdx.y + R) * T::SW + threadIdx.x + R;
   float ck[C], lk[C], acc[C];
 #pragma unroll
   for (int ch = 0; ch < C; ++ch) {
-    ck[ch] = sc[ch * T::PLANE + cen];
-    lk[ch] = sl[ch * T::PLANE + cen];
+    ck[ch] = sm[cen * REC + ch];
+    lk[ch] = sm[cen * REC + C + ch];
     acc[ch] = 0.0f;
   }
   const float ec20 = 20.0f * ec;
@@ -168,14 +185,24 @@ __device__ __forceinline__ void wide_adjoint_body(float* __restrict__ sm, float*
 #pragma unroll 1
     for (int dx = -R; dx <= R; ++dx) {
       const int e = cen + dy * T::SW + dx;
+      const float4* rec = reinterpret_cast<const float4*>(sm + e * REC);
+      float v[4 * NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const float4 t = rec[q];
+        v[4 * q] = t.x;
+        v[4 * q + 1] = t.y;
+        v[4 * q + 2] = t.z;
+        v[4 * q + 3] = t.w;
+      }
       float d[C], dl[C];
       // each channel sum in four independent chains (latency of the FMA chains)
       float s2p[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       float lp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) {
-        d[ch] = sc[ch * T::PLANE + e] - ck[ch];
-        dl[ch] = sl[ch * T::PLANE + e] - lk[ch];
+        d[ch] = v[ch] - ck[ch];
+        dl[ch] = v[C + ch] - lk[ch];
         s2p[ch & 3] = fmaf(d[ch], d[ch], s2p[ch & 3]);
         pp[ch & 3] = fmaf(d[ch], dl[ch], pp[ch & 3]);
         lp[ch & 3] = fmaf(lk[ch], d[ch], lp[ch & 3]);
@@ -188,8 +215,8 @@ __device__ __forceinline__ void wide_adjoint_body(float* __restrict__ sm, float*
       float ph = (t2 * t2) * fmaf(-4.0f, t, 5.0f);
       float dph = t3 * (t - 1.0f);                       // phi' / 20
       if constexpr (BORDER) {
-        ph *= mask[e];
-        dph *= mask[e];
+        ph *= v[2 * C];
+        dph *= v[2 * C];
       }
       const float coef = (dph * ec20) * proj;
 #pragma unroll
