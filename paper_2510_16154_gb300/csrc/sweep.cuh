@@ -199,9 +199,16 @@ forward_tile_kernel(const float* __restrict__ c, float* __restrict__ out,
 // (J_F^T lam)_k = (1/M) sum_{j in W(k)} [phi'(r) eps_c delta (delta . dlam) + phi(r) dlam],
 //   delta = c_j - c_k, dlam = lam_j - lam_k (gather form: the Jacobian blocks are
 //   symmetric because r_kj = r_jk, the window is symmetric and M is constant);
-// D_x partial = sum_k sum_j phi'(r_kj) |x_j - x_k|^2 (lam_k . delta),
-// D_c partial = sum_k sum_j phi'(r_kj) |delta|^2     (lam_k . delta)   (times 1/(2M) later).
-// phi' = 20 t^3 (t - 1) with t = max(1 - r, 0); the factor 20 is applied once per thread.
+// D_x = sum_k sum_j phi'(r_kj) |x_j - x_k|^2 (lam_k . delta) (times 1/(2M) later), and
+// D_c likewise with |delta|^2.  phi' and both distances are symmetric in (k, j), delta is
+// antisymmetric and the window is symmetric, so pairing (k, j) with (j, k) gives
+//   D_x = -1/2 sum_k sum_j phi'(r_kj) |x_j - x_k|^2 (delta . dlam),
+// which reuses delta . dlam (already needed for J^T lam) instead of a third dot product
+// lam_k . delta, and adds each pair's contribution once instead of as two nearly
+// cancelling terms.  The identity holds for the image total, which is what D is; a
+// block's partial alone has no meaning.
+// phi' = 20 t^3 (t - 1) with t = max(1 - r, 0); the factor -20/2 is applied once per
+// thread.
 template <class T, int R, int C, int PXH, bool BORDER>
 __device__ __forceinline__ void adjoint_body(const float2* __restrict__ sm,
                                              const float2* __restrict__ smask,
@@ -213,8 +220,13 @@ __device__ __forceinline__ void adjoint_body(const float2* __restrict__ sm,
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int sx = tx * PXH;
   float2 lk[PXH][C], nck[PXH][C], nlk[PXH][C], acc[PXH][C];
+  // Validity of the thread's own pixels (border tiles): the paired D terms of a pixel
+  // outside the image are not zero by themselves (its zero-filled lam_k makes
+  // dlam = lam_j), so they are masked like those of a neighbour outside the image.
+  float2 vk[BORDER ? PXH : 1];
 #pragma unroll
-  for (int p = 0; p < PXH; ++p)
+  for (int p = 0; p < PXH; ++p) {
+    if constexpr (BORDER) vk[p] = smask[(ty + R) * T::SW + sx + R + p];
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) {
       const int o = ch * T::PLANE + (ty + R) * T::SW + sx + R + p;
@@ -224,6 +236,7 @@ __device__ __forceinline__ void adjoint_body(const float2* __restrict__ sm,
       nlk[p][ch] = make_float2(-lk[p][ch].x, -lk[p][ch].y);
       acc[p][ch] = f2(0.0f);
     }
+  }
   const float2 nkc = f2(-kc), m4 = f2(-4.0f), five = f2(5.0f), m1 = f2(-1.0f);
   const float2 ec20 = f2(20.0f * ec);
   float2 Dx = f2(0.0f), Dc = f2(0.0f);
@@ -255,12 +268,10 @@ __device__ __forceinline__ void adjoint_body(const float2* __restrict__ sm,
         }
         float2 s2 = __fmul2_rn(d[0], d[0]);
         float2 proj = __fmul2_rn(d[0], dl[0]);
-        float2 lkd = __fmul2_rn(lk[p][0], d[0]);
 #pragma unroll
         for (int ch = 1; ch < C; ++ch) {
           s2 = __ffma2_rn(d[ch], d[ch], s2);
           proj = __ffma2_rn(d[ch], dl[ch], proj);
-          lkd = __ffma2_rn(lk[p][ch], d[ch], lkd);
         }
         const float2 t = max0(__ffma2_rn(nkc, s2, sp));        // max(1 - r, 0)
         const float2 t2 = __fmul2_rn(t, t);
@@ -268,16 +279,17 @@ __device__ __forceinline__ void adjoint_body(const float2* __restrict__ sm,
         float2 ph = __fmul2_rn(__fmul2_rn(t2, t2), __ffma2_rn(m4, t, five));
         float2 dph = __fmul2_rn(t3, __fadd2_rn(t, m1));         // phi' / 20
         if constexpr (BORDER) {
-          ph = __fmul2_rn(ph, mseg[e]);
-          dph = __fmul2_rn(dph, mseg[e]);
+          const float2 m = __fmul2_rn(mseg[e], vk[p]);
+          ph = __fmul2_rn(ph, m);
+          dph = __fmul2_rn(dph, m);
         }
-        const float2 coef = __fmul2_rn(__fmul2_rn(dph, ec20), proj);
+        const float2 gk = __fmul2_rn(dph, proj);
+        const float2 coef = __fmul2_rn(gk, ec20);
 #pragma unroll
         for (int ch = 0; ch < C; ++ch) {
           acc[p][ch] = __ffma2_rn(coef, d[ch], acc[p][ch]);
           acc[p][ch] = __ffma2_rn(ph, dl[ch], acc[p][ch]);
         }
-        const float2 gk = __fmul2_rn(dph, lkd);
         Dx = __ffma2_rn(gk, d2, Dx);
         Dc = __ffma2_rn(gk, s2, Dc);
       }
@@ -285,7 +297,7 @@ __device__ __forceinline__ void adjoint_body(const float2* __restrict__ sm,
   }
   store_pairs<T, C, PXH>(out, g, lk, acc, x0, y0);
   __shared__ double red[2 * 32];
-  double v[2] = {20.0 * ((double)Dx.x + (double)Dx.y), 20.0 * ((double)Dc.x + (double)Dc.y)};
+  double v[2] = {-10.0 * ((double)Dx.x + (double)Dx.y), -10.0 * ((double)Dc.x + (double)Dc.y)};
   double tot[2];
   block_sum<2>(v, red, tot);
   if (threadIdx.x == 0 && threadIdx.y == 0) {   // partial points at this tile's pair

@@ -42,7 +42,8 @@ __global__ void forward_generic_kernel(const float* __restrict__ c, float* __res
                         blockIdx.y * blockDim.y + threadIdx.y);
 }
 
-// One pixel of the adjoint step; returns its D partial sums in Dx, Dc.
+// One pixel of the adjoint step; returns its D partial sums in Dx, Dc (the paired form
+// of adjoint_body: the caller scales them by -1/2).
 __device__ __forceinline__ void adjoint_generic_pixel(const float* __restrict__ c,
                                                       const float* __restrict__ lam,
                                                       float* __restrict__ out,
@@ -69,23 +70,22 @@ __device__ __forceinline__ void adjoint_generic_pixel(const float* __restrict__ 
         const size_t j = (size_t)y * g.W + x;
         const float* cj = c + j * C;
         const float* lj = lam + j * C;
-        float s2 = 0.0f, proj = 0.0f, lkd = 0.0f;
+        float s2 = 0.0f, proj = 0.0f;
         for (int ch = 0; ch < C; ++ch) {
           const float d = cj[ch] - ck[ch];
           s2 = fmaf(d, d, s2);
           proj = fmaf(d, lj[ch] - lk[ch], proj);
-          lkd = fmaf(lk[ch], d, lkd);
         }
         const float sp = fmaf(kx, (float)(dx * dx), ky * (float)(dy * dy));
         float ph, dph;
         wendland_phi_dphi(fmaf(kc, s2, sp), ph, dph);
-        const float coef = (dph * ec) * proj;
+        const float gk = dph * proj;      // D in the paired form of adjoint_body
+        const float coef = gk * ec;
         for (int ch = 0; ch < C; ++ch) {
           const float d = cj[ch] - ck[ch];
           acc[ch] = fmaf(coef, d, acc[ch]);
           acc[ch] = fmaf(ph, lj[ch] - lk[ch], acc[ch]);
         }
-        const float gk = dph * lkd;
         const float d2 = fmaf(g.inv_w2, (float)(dx * dx), g.inv_h2 * (float)(dy * dy));
         Dx = fmaf(gk, d2, Dx);
         Dc = fmaf(gk, s2, Dc);
@@ -104,7 +104,7 @@ __global__ void adjoint_generic_kernel(const float* __restrict__ c,
   adjoint_generic_pixel(c, lam, out, eps_n, g, blockIdx.x * blockDim.x + threadIdx.x,
                         blockIdx.y * blockDim.y + threadIdx.y, Dx, Dc);
   __shared__ double red[2 * 32];
-  double v[2] = {(double)Dx, (double)Dc};
+  double v[2] = {-0.5 * (double)Dx, -0.5 * (double)Dc};
   double tot[2];
   block_sum<2>(v, red, tot);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -158,7 +158,7 @@ __global__ void adjoint_generic_batch_kernel(const BatchSweepImg* __restrict__ i
     float Dx, Dc;
     adjoint_generic_pixel(cn, lin, lout, im.eps + 2 * n, g, job.tx * blockDim.x + threadIdx.x,
                           job.ty * blockDim.y + threadIdx.y, Dx, Dc);
-    double v[2] = {(double)Dx, (double)Dc};
+    double v[2] = {-0.5 * (double)Dx, -0.5 * (double)Dc};
     double tot[2];
     block_sum<2>(v, red, tot);
     if (threadIdx.x == 0 && threadIdx.y == 0) {

@@ -198,18 +198,15 @@ __device__ __forceinline__ void wide_adjoint_body(float* __restrict__ sm, float*
       float d[C], dl[C];
       // each channel sum in four independent chains (latency of the FMA chains)
       float s2p[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      float lp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) {
         d[ch] = v[ch] - ck[ch];
         dl[ch] = v[C + ch] - lk[ch];
         s2p[ch & 3] = fmaf(d[ch], d[ch], s2p[ch & 3]);
         pp[ch & 3] = fmaf(d[ch], dl[ch], pp[ch & 3]);
-        lp[ch & 3] = fmaf(lk[ch], d[ch], lp[ch & 3]);
       }
       const float s2 = (s2p[0] + s2p[1]) + (s2p[2] + s2p[3]);
       const float proj = (pp[0] + pp[1]) + (pp[2] + pp[3]);
-      const float lkd = (lp[0] + lp[1]) + (lp[2] + lp[3]);
       const float t = fmaxf(fmaf(-kc, s2, fmaf(-kx, (float)(dx * dx), sy)), 0.0f);
       const float t2 = t * t, t3 = t2 * t;
       float ph = (t2 * t2) * fmaf(-4.0f, t, 5.0f);
@@ -218,18 +215,23 @@ __device__ __forceinline__ void wide_adjoint_body(float* __restrict__ sm, float*
         ph *= v[2 * C];
         dph *= v[2 * C];
       }
-      const float coef = (dph * ec20) * proj;
+      const float gk = dph * proj;        // D in the paired form of adjoint_body
+      const float coef = gk * ec20;
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) acc[ch] = fmaf(ph, dl[ch], fmaf(coef, d[ch], acc[ch]));
-      const float gk = dph * lkd;
       Dx = fmaf(gk, fmaf(g.inv_w2, (float)(dx * dx), d2y), Dx);
       Dc = fmaf(gk, s2, Dc);
     }
   }
 #pragma unroll
   for (int ch = 0; ch < C; ++ch) acc[ch] = fmaf(g.scale, acc[ch], lk[ch]);
+  if constexpr (BORDER) {
+    // a pixel outside the image has zero-filled lam_k, so its paired D terms
+    // (delta . lam_j) are not zero by themselves: drop them
+    if (sm[cen * REC + 2 * C] == 0.0f) Dx = Dc = 0.0f;
+  }
   __shared__ double red[2 * 32];
-  double v[2] = {20.0 * (double)Dx, 20.0 * (double)Dc};
+  double v[2] = {-10.0 * (double)Dx, -10.0 * (double)Dc};
   double tot[2];
   block_sum<2>(v, red, tot);
   if (threadIdx.x == 0 && threadIdx.y == 0) {

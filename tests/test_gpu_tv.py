@@ -114,6 +114,24 @@ def test_objective_and_terminal_adjoint(H, W, C, tv_mode):
     assert np.max(np.abs(got - want)) <= 1e-5 * max(np.max(np.abs(want)), 1e-30)
 
 
+@pytest.mark.parametrize("tv_mode", [0, 1])
+@pytest.mark.parametrize("H,W,C", SHAPES + [(517, 391, 3), (300, 1030, 1)])
+def test_terminal_objective_equals_trial_objective_bitwise(H, W, C, tv_mode):
+    # Algorithm 1 compares the L~ that comes with the terminal adjoint against the L~ of
+    # each Armijo trial (objective only): for the same fields they must be the same
+    # float64 number, or rounding alone could accept or reject a trial.
+    ensure_lib()
+    rng = np.random.default_rng(H * 11 + W + 3 * C)
+    c0, c, v, mu, _ = _inputs(rng, H, W, C)
+    p, _ = params(H, W, C, 2, 1, alpha=300.0, rho=0.2, tv_mode=tv_mode)
+    with lib.Context(p, dev(c0, np.float32)) as ctx:
+        cd, vd, md = dev(c, np.float32), dev(v, np.float32), dev(mu, np.float32)
+        with_lam, without = np.zeros(1), np.zeros(1)
+        lib.agents_objective(ctx.handle, cd, vd, md, with_lam, zeros_dev(H, W, C))
+        lib.agents_objective(ctx.handle, cd, vd, md, without, None)
+    assert with_lam[0] == without[0]
+
+
 def test_full_size_tv_kernels():
     # the 1024 x 1024 x 3 fields of the throughput benchmark
     ensure_lib()
