@@ -123,6 +123,14 @@ int ws_net_adam_step(ws_net* net, float lr, float beta1, float beta2, float adam
 /* Message of the last failure on the calling thread ("" if none). */
 const char* ws_last_error(void);
 
+/* Convolutions whose image width is at least 128 and whose channel counts are multiples
+ * of 16 (the output count at most 128 or a multiple of 128) run on the tcgen05 tensor
+ * cores with tensor-memory accumulators; every wait inside those kernels is bounded, and
+ * a kernel that gives up writes NaN to its outputs and raises a device-side flag.
+ * Returns 1 if the flag was raised since the last call (and clears it), 0 if not,
+ * AGENTS_ECUDA if it could not be read.  Synchronises the device. */
+int ws_tensor_core_fault_take(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -117,6 +117,7 @@ _SIGNATURES = {
     "ws_conv3x3_backward_weight_workspace": (ctypes.c_size_t, [c_int32, c_int32, c_int32,
                                                                c_int32, c_int32]),
     "ws_transpose_weights": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p]),
+    "ws_tensor_core_fault_take": (c_int, []),
     "ws_net_create": (c_int, [POINTER(ws_net_config), c_void_p, POINTER(c_void_p)]),
     "ws_net_destroy": (None, [c_void_p]),
     "ws_net_num_params": (ctypes.c_int64, [c_void_p]),
@@ -402,3 +403,11 @@ def ws_conv3x3_backward_weight(x, dy, dw, db, N, H, W, Cin, Cout, workspace, up=
 def ws_transpose_weights(w, w16, wt16, Cin, Cout, stream=None):
     _ws_check(load().ws_transpose_weights(_ptr(w, "float32"), _ptr(w16), _ptr(wt16), Cin, Cout,
                                           _stream(stream)), "ws_transpose_weights")
+
+
+def ws_tensor_core_fault_take() -> bool:
+    """True if a tensor-core convolution gave up a bounded wait since the last call."""
+    r = load().ws_tensor_core_fault_take()
+    if r < 0:
+        _ws_check(r, "ws_tensor_core_fault_take")
+    return r == 1

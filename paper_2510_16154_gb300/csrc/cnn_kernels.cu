@@ -414,6 +414,8 @@ static int grid_1d(size_t n, int threads = 256) {
 cudaError_t conv_forward(const float* x, const __nv_bfloat16* w16, const float* bias, float* y,
                          const float* add, float* y2, int N, int H, int W, int Cin, int Cout,
                          int relu, int up, cudaStream_t s) {
+  if (conv_tc_applies(W, Cin, Cout))
+    return conv_forward_tc(x, w16, bias, y, add, y2, N, H, W, Cin, Cout, relu, up, s);
   GemmArgs g{};
   g.mode = 0;
   g.N = N; g.H = H; g.W = W; g.Cin = Cin; g.Cout = Cout; g.up = up;
@@ -426,6 +428,8 @@ cudaError_t conv_forward(const float* x, const __nv_bfloat16* w16, const float* 
 
 cudaError_t conv_backward_data(const float* dy, const __nv_bfloat16* wt16, float* dx, int N, int H,
                                int W, int Cin, int Cout, cudaStream_t s) {
+  if (conv_tc_applies(W, Cout, Cin))
+    return conv_backward_data_tc(dy, wt16, dx, N, H, W, Cin, Cout, s);
   GemmArgs g{};
   g.mode = 1;
   g.N = N; g.H = H; g.W = W; g.Cin = Cin; g.Cout = Cout; g.up = 0;

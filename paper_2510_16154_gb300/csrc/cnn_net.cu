@@ -585,6 +585,12 @@ int ws_conv3x3_backward_weight(const float* x, const float* dy, float* dw, float
   return AGENTS_OK;
 }
 
+int ws_tensor_core_fault_take(void) {
+  const int r = ws::conv_tc_take_error();
+  if (r < 0) return ws_fail(AGENTS_ECUDA, "ws_tensor_core_fault_take: cannot read the flag");
+  return r;
+}
+
 int ws_transpose_weights(const float* w, uint16_t* w16, uint16_t* wt16, int32_t Cin, int32_t Cout,
                          void* stream) {
   if (!w || !w16 || Cin < 1 || Cout < 1)

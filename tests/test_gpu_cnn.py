@@ -44,6 +44,10 @@ def _bound(ref_abs, K):
 CONV_CASES = [  # N, H, W, Cin, Cout, up
     (2, 13, 11, 3, 6, 0), (2, 9, 20, 16, 40, 0), (1, 16, 12, 24, 32, 1), (3, 8, 8, 64, 8, 0),
     (1, 6, 34, 8, 72, 1),
+    # width >= 128, channel counts multiples of 16: the tcgen05 kernel (ragged last
+    # segment, 2x upsampled input, two 128-channel output tiles, 16 K groups, N = 16)
+    (1, 3, 200, 16, 32, 0), (2, 4, 128, 32, 64, 1), (1, 2, 300, 48, 256, 0),
+    (1, 3, 130, 128, 16, 0),
 ]
 
 
@@ -68,6 +72,7 @@ def test_conv_forward(case):
     got = host(y).astype(np.float64)
     assert np.all(np.abs(got - ref) <= _bound(ref_abs, 9 * Cin + 1))
     assert np.all(np.abs(host(y2) - (got + add)) <= 1e-6 * (np.abs(got) + np.abs(add)))
+    assert not lib.ws_tensor_core_fault_take()
 
 
 @pytest.mark.parametrize("case", CONV_CASES)
@@ -87,6 +92,7 @@ def test_conv_backward_data_and_weight(case):
     dx = torch.empty(N, H, W, Cin, device="cuda")
     lib.ws_conv3x3_backward_data(dev(dy, np.float32), wt16, dx, N, H, W, Cin, Cout)
     assert np.all(np.abs(host(dx) - dx_ref) <= _bound(dxa, 9 * Cout))
+    assert not lib.ws_tensor_core_fault_take()
 
     ws = torch.empty(lib.ws_conv3x3_backward_weight_workspace(N, H, W, Cin, Cout) // 4 + 1,
                      device="cuda")
@@ -126,15 +132,20 @@ def test_network_layout_matches_oracle():
     net.close()
 
 
-# (levels, base, mu, z, loss, gradient, worst block) tolerances
-NET_TOL = [(3, 8, 3e-3, 1e-4, 1e-4, 2e-3, 1e-2), (4, 16, 1e-2, 1e-3, 2e-3, 2e-2, 5e-2)]
+# (levels, base, N, H, W) and the (mu, z, loss, gradient, worst block) tolerances.  The
+# third case is 128 pixels wide, so its level-1 convolutions other than the first and the
+# head run on the tcgen05 kernel (forward and backward-data); the same noise injection
+# gives 2.7e-3 (mu), 6e-7 (z), 3.2e-5 (loss), 7.8e-4 (gradient), 1.7e-3 (worst block).
+NET_TOL = [(3, 8, 2, 16, 24, 3e-3, 1e-4, 1e-4, 2e-3, 1e-2),
+           (4, 16, 2, 16, 24, 1e-2, 1e-3, 2e-3, 2e-2, 5e-2),
+           (2, 16, 1, 8, 128, 1e-2, 1e-4, 1e-4, 3e-3, 6e-3)]
 
 
-@pytest.mark.parametrize("levels,base,t_mu,t_z,t_loss,t_g,t_block", NET_TOL)
-def test_network_forward_and_gradient_against_oracle(levels, base, t_mu, t_z, t_loss, t_g,
-                                                     t_block):
+@pytest.mark.parametrize("levels,base,N,H,W,t_mu,t_z,t_loss,t_g,t_block", NET_TOL)
+def test_network_forward_and_gradient_against_oracle(levels, base, N, H, W, t_mu, t_z, t_loss,
+                                                     t_g, t_block):
     ensure_lib()
-    cfg, net, theta, x, mu_t, le_t = _net_case(levels=levels, base=base, H=16, W=24)
+    cfg, net, theta, x, mu_t, le_t = _net_case(levels=levels, base=base, N=N, H=H, W=W)
     mu, z = net.raw(dev(x, np.float32))
     mu_ref, z_ref, _ = cnn.net_forward(cfg, theta, x)
     err_mu = np.linalg.norm(host(mu) - mu_ref) / np.linalg.norm(mu_ref)
@@ -157,6 +168,7 @@ def test_network_forward_and_gradient_against_oracle(levels, base, t_mu, t_z, t_
         a, b = gg[off:off + n], g_ref[off:off + n]
         assert np.linalg.norm(a - b) <= t_block * np.linalg.norm(b) + 1e-9, name
         off += n
+    assert not lib.ws_tensor_core_fault_take()
     net.close()
 
 
