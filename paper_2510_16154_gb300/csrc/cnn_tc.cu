@@ -1,25 +1,27 @@
 // 3x3 convolutions of the warm-start network on the fifth-generation tensor cores
 // (tcgen05.mma, kind::f16, bfloat16 operands, float32 accumulators in tensor memory).
 //
-// A CTA computes a 128-pixel segment of one output row for NT output channels:
-//   Y[m][n] = sum_{tap} sum_{c} X[pixel(m) + offset(tap)][c] W[n][tap][c].
-// The 3x3 taps read the same three input rows at shifted columns, so the input is staged
-// once per 16-channel K group as a patch of 3 rows x 130 pixels (the segment and one pixel
-// either side) in the canonical K-major layout without swizzle: for each row and each
-// group of 8 channels, 130 pixel slots of 16 bytes (8 bfloat16), consecutive pixels 16
-// bytes apart.  An 8-pixel core matrix is then 128 contiguous bytes, 8-pixel groups are
+// A CTA computes a 128-pixel segment of up to kRows (4) consecutive output rows for NT output
+// channels:  Y[m][n] = sum_{tap} sum_{c} X[pixel(m) + offset(tap)][c] W[n][tap][c].
+// The 3x3 taps read the same input rows at shifted columns, so the input is staged once
+// per 16-channel K group as a patch of kRows + 2 rows x 130 pixels (the segment and one
+// pixel either side) in the canonical K-major layout without swizzle: for each row and
+// each group of 8 channels, 130 pixel slots of 16 bytes (8 bfloat16), consecutive pixels
+// 16 bytes apart.  An 8-pixel core matrix is then 128 contiguous bytes, 8-pixel groups are
 // 128 bytes apart (the descriptor's M stride) and the two 8-channel halves of a K step are
-// one plane apart (its K stride), so the A operand of tap (ky, kx) is the same patch with
-// the descriptor's start moved by a row plane and kx slots: nine MMAs per K group, no
-// im2col copy.  The weights of the K group are staged as 9 taps x 2 halves x NT rows of
-// 16 bytes (the B operand, K-major).
+// one plane apart (its K stride), so the A operand of output row r and tap (ky, kx) is the
+// same patch with the descriptor's start moved by r + ky row planes and kx slots: nine
+// MMAs per row and K group, no im2col copy.  The weights of the K group are staged once
+// for all rows as 9 taps x 2 halves x NT rows of 16 bytes (the B operand, K-major); each
+// output row accumulates in its own NT columns of tensor memory.
 // Two stage buffers alternate: while the tensor core works on one K group the threads
 // stage the next; a buffer is refilled only after the tcgen05.commit of the MMAs that read
-// it has arrived on its mbarrier.  One thread issues the MMAs; the accumulator (128 lanes x
-// NT columns of float32) is read back with tcgen05.ld by the four warps (warp w owns lanes
-// 32w..32w+31, i.e. pixels 32w..32w+31 of the segment) for the bias/ReLU/skip epilogue.
+// it has arrived on its mbarrier.  One thread issues the MMAs; the accumulators (128 lanes
+// x NT columns of float32 per row) are read back with tcgen05.ld: warp w reads lanes
+// 32 (w mod 4) .. +31 (pixels of the segment) and every other 16-column chunk, starting at
+// chunk w / 4, for the bias/ReLU/skip epilogue.
 // Every wait is bounded: a wait that gives up sets tc_error and the CTA writes NaN to its
-// outputs instead of the accumulator, so a failure cannot pass silently.
+// outputs instead of the accumulators, so a failure cannot pass silently.
 //
 // Forward:        X = x (read through nearest 2x upsampling when up = 1), W = w16
 //                 [Cout][9][Cin], offset(tap) = (ky - 1, kx - 1).
@@ -37,9 +39,10 @@ namespace {
 
 constexpr int kTcM = 128;                 // pixels per CTA (MMA M)
 constexpr int kTcSlots = kTcM + 2;        // patch columns x0 - 1 .. x0 + 128
-constexpr int kTcThreads = 128;
+constexpr int kRows = 4;                  // output rows per CTA
+constexpr int kTcThreads = 256;
 constexpr int kPlane = kTcSlots * 16;     // bytes of one (row, 8-channel half) patch plane
-constexpr int kPatchBytes = 3 * 2 * kPlane;
+constexpr int kPatchBytes = (kRows + 2) * 2 * kPlane;
 constexpr int kHeader = 128;              // mbarriers and the TMEM address
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
@@ -51,6 +54,7 @@ struct TcArgs {
   int CI, CO;          // input channels (K per tap), output channels
   int up;              // forward: input read through nearest 2x upsampling
   int nt;              // output channels per CTA
+  int rows;            // output rows per CTA (1..kRows)
   const float* x;      // forward: x [N][H >> up][W >> up][CI]; backward-data: dy [N][H][W][CI]
   const __nv_bfloat16* w;  // [CO][9][CI]
   const float* bias;
@@ -139,16 +143,20 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 
 __host__ __device__ constexpr int stage_bytes(int nt) { return kPatchBytes + 9 * 2 * nt * 16; }
 
-// TMEM columns to allocate: a power of two >= 32 holding nt float32 columns.
-__host__ __device__ constexpr int tmem_cols(int nt) { return nt <= 32 ? 32 : nt <= 64 ? 64 : nt <= 128 ? 128 : 256; }
+// TMEM columns to allocate: a power of two >= 32 holding kRows x nt float32 columns.
+__host__ __device__ constexpr int tmem_cols(int nt) {
+  return kRows * nt <= 32 ? 32 : kRows * nt <= 64 ? 64 : kRows * nt <= 128 ? 128 : kRows * nt <= 256 ? 256 : 512;
+}
 
 __global__ void __launch_bounds__(kTcThreads) tc_conv_kernel(TcArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int segs = (g.W + kTcM - 1) / kTcM;
-  const int row = blockIdx.x / segs;                 // img * H + output row
-  const int x0 = (blockIdx.x - row * segs) * kTcM;
-  const int img = row / g.H, py = row - img * g.H;
+  const int rblocks = (g.H + g.rows - 1) / g.rows;
+  const int seg = blockIdx.x % segs, rb = blockIdx.x / segs;   // rb = img * rblocks + row block
+  const int img = rb / rblocks, py0 = (rb - img * rblocks) * g.rows;
+  const int nrows = min(g.rows, g.H - py0);
+  const int x0 = seg * kTcM;
   const int n0 = blockIdx.y * g.nt;
   const int nt = g.nt;
   const int stages = g.CI / 16;
@@ -187,10 +195,10 @@ __global__ void __launch_bounds__(kTcThreads) tc_conv_kernel(TcArgs g) {
       if (__syncthreads_or(!mine)) { ok = false; break; }
     }
     const int c0 = s * 16;
-    // patch: 3 rows x 130 slots, 16 channels each -> two 16-byte halves
-    for (int it = tid; it < 3 * kTcSlots; it += kTcThreads) {
+    // patch: nrows + 2 rows x 130 slots, 16 channels each -> two 16-byte halves
+    for (int it = tid; it < (nrows + 2) * kTcSlots; it += kTcThreads) {
       const int rr = it / kTcSlots, sl = it - rr * kTcSlots;
-      const int yy = py + rr - 1, xx = x0 + sl - 1;
+      const int yy = py0 + rr - 1, xx = x0 + sl - 1;
       uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
       if (yy >= 0 && yy < g.H && xx >= 0 && xx < g.W) {
         const float* p = g.x + (((size_t)img * Hs + (yy >> g.up)) * Ws + (xx >> g.up)) * g.CI + c0;
@@ -220,13 +228,16 @@ __global__ void __launch_bounds__(kTcThreads) tc_conv_kernel(TcArgs g) {
       fence_after_sync();
       const uint32_t pa = smem_addr(st), pw = smem_addr(wb);
 #pragma unroll 1
-      for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap - 3 * ky;
-        const int rr = g.mode == 0 ? ky : 2 - ky;
-        const int sx = g.mode == 0 ? kx : 2 - kx;
-        const uint64_t ad = smem_desc(pa + rr * 2 * kPlane + sx * 16, kPlane, 128);
-        const uint64_t bd = smem_desc(pw + tap * 2 * nt * 16, nt * 16, 128);
-        mma_f16(tmem, ad, bd, idesc, (s > 0 || tap > 0) ? 1u : 0u);
+      for (int r = 0; r < nrows; ++r) {
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+          const int ky = tap / 3, kx = tap - 3 * ky;
+          const int rr = r + (g.mode == 0 ? ky : 2 - ky);
+          const int sx = g.mode == 0 ? kx : 2 - kx;
+          const uint64_t ad = smem_desc(pa + rr * 2 * kPlane + sx * 16, kPlane, 128);
+          const uint64_t bd = smem_desc(pw + tap * 2 * nt * 16, nt * 16, 128);
+          mma_f16(tmem + (uint32_t)(r * nt), ad, bd, idesc, (s > 0 || tap > 0) ? 1u : 0u);
+        }
       }
       mma_commit(smem_addr(&bars[b]));
     }
@@ -239,46 +250,55 @@ __global__ void __launch_bounds__(kTcThreads) tc_conv_kernel(TcArgs g) {
   }
   fence_after_sync();
 
-  // epilogue: thread = pixel x0 + tid, 16 accumulator columns at a time
-  const int px = x0 + tid;
+  // epilogue: thread = pixel x0 + 32 (warp mod 4) + lane, 16 accumulator columns at a time
+  const int quarter = warp & 3, half = warp >> 2;
+  const int px = x0 + quarter * 32 + (tid & 31);
   const bool valid = px < g.W;
-  const size_t pix = ((size_t)img * g.H + py) * g.W + px;
   if (ok) {
-    for (int c = 0; c < nt; c += 16) {
-      uint32_t r[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
-      if (!valid) continue;
-      float o[16];
+    for (int r = 0; r < nrows; ++r) {
+      const size_t pix = ((size_t)img * g.H + py0 + r) * g.W + px;
+      for (int c = half * 16; c < nt; c += 32) {
+        uint32_t v[16];
+        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * nt + c), v);
+        if (!valid) continue;
+        float o[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        float v = __uint_as_float(r[i]);
-        if (g.mode == 0) {
-          if (g.bias) v += __ldg(g.bias + n0 + c + i);
-          if (g.relu) v = fmaxf(v, 0.0f);
+        for (int i = 0; i < 16; ++i) {
+          float a = __uint_as_float(v[i]);
+          if (g.mode == 0) {
+            if (g.bias) a += __ldg(g.bias + n0 + c + i);
+            if (g.relu) a = fmaxf(a, 0.0f);
+          }
+          o[i] = a;
         }
-        o[i] = v;
-      }
-      float* yo = g.y + pix * g.CO + n0 + c;
+        float* yo = g.y + pix * g.CO + n0 + c;
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        reinterpret_cast<float4*>(yo)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-      if (g.mode == 0 && g.add) {
-        const float* ad = g.add + pix * g.CO + n0 + c;
-        float* y2 = g.y2 + pix * g.CO + n0 + c;
+        for (int q = 0; q < 4; ++q)
+          reinterpret_cast<float4*>(yo)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        if (g.mode == 0 && g.add) {
+          const float4* ad = reinterpret_cast<const float4*>(g.add + pix * g.CO + n0 + c);
+          float4* y2 = reinterpret_cast<float4*>(g.y2 + pix * g.CO + n0 + c);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) y2[i] = o[i] + __ldg(ad + i);
+          for (int q = 0; q < 4; ++q) {
+            const float4 a = __ldg(ad + q);
+            y2[q] = make_float4(o[4 * q] + a.x, o[4 * q + 1] + a.y, o[4 * q + 2] + a.z, o[4 * q + 3] + a.w);
+          }
+        }
       }
     }
   } else {
     if (tid == 0) atomicExch(&tc_error, 1);
-    if (valid) {
-      for (int c = 0; c < nt; ++c) {
-        g.y[pix * g.CO + n0 + c] = __int_as_float(0x7fc00000);
-        if (g.mode == 0 && g.add) g.y2[pix * g.CO + n0 + c] = __int_as_float(0x7fc00000);
+    if (valid && half == 0) {
+      for (int r = 0; r < nrows; ++r) {
+        const size_t pix = ((size_t)img * g.H + py0 + r) * g.W + px;
+        for (int c = 0; c < nt; ++c) {
+          g.y[pix * g.CO + n0 + c] = __int_as_float(0x7fc00000);
+          if (g.mode == 0 && g.add) g.y2[pix * g.CO + n0 + c] = __int_as_float(0x7fc00000);
+        }
       }
     }
     // MMAs may still be in flight: give the last commit one more bounded wait before the
-    // accumulator's columns are released.
+    // accumulators' columns are released.
     if (issued > 0) {
       const int s = issued - 1;
       mbar_wait(smem_addr(&bars[s & 1]), (uint32_t)((s >> 1) & 1));
@@ -301,21 +321,20 @@ int tc_tile_n(int co) {
   return co % 128 == 0 ? 128 : 0;
 }
 
-// Shared memory of a CTA: header, two stage buffers and a guard region, so that every
-// address the descriptors of a stage can reach (including the 15 stride steps past the
-// start of the last tap's window) lies inside the allocation.
-size_t tc_smem_bytes(int nt) { return (size_t)kHeader + 2 * (size_t)stage_bytes(nt) + 32768; }
+// Shared memory of a CTA: header and two stage buffers.  Every address a descriptor of a
+// stage reaches (the start, 15 M-stride steps and one K-stride step) lies inside that
+// stage: the last row's last tap ends exactly at the end of the patch, the last tap's
+// weights at the end of the stage.
+size_t tc_smem_bytes(int nt) { return (size_t)kHeader + 2 * (size_t)stage_bytes(nt); }
 
-cudaError_t launch_tc(const TcArgs& g, int N, cudaStream_t s) {
+cudaError_t launch_tc(TcArgs g, int N, cudaStream_t s) {
   const size_t smem = tc_smem_bytes(g.nt);
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
-  const long long blocks = (long long)((g.W + kTcM - 1) / kTcM) * N * g.H;
+  // kRows output rows per CTA: each staged weight group serves kRows x 9 MMAs.  (Fewer
+  // rows on small grids, for more CTAs, measured slower: 2.70 against 2.36 ms for the
+  // network at 1024 x 1024, where the deep layers' weight staging dominates.)
+  const long long segs = (g.W + kTcM - 1) / kTcM;
+  g.rows = kRows;
+  const long long blocks = segs * N * ((g.H + g.rows - 1) / g.rows);
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)blocks, g.CO / g.nt);
   tc_conv_kernel<<<grid, kTcThreads, smem, s>>>(g);

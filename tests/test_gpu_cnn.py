@@ -48,6 +48,8 @@ CONV_CASES = [  # N, H, W, Cin, Cout, up
     # segment, 2x upsampled input, two 128-channel output tiles, 16 K groups, N = 16)
     (1, 3, 200, 16, 32, 0), (2, 4, 128, 32, 64, 1), (1, 2, 300, 48, 256, 0),
     (1, 3, 130, 128, 16, 0),
+    # enough CTAs for four output rows per CTA (the last row block holds two)
+    (1, 610, 256, 16, 32, 0),
 ]
 
 
