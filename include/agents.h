@@ -93,7 +93,8 @@ const char* agents_last_error(const agents_ctx* ctx);
  *   c^{n+1}_i = c^n_i + dt/M sum_{j in W(i)} phi(r_ij)(c^n_j - c^n_i),
  *   r_ij = eps_x^n/2 |x_j - x_i|^2 + eps_c^n/2 |c^n_j - c^n_i|^2,
  *   phi(r) = (1 - r)^4 (4r + 1) on [0,1], 0 beyond (the C2 Wendland kernel of Eq. kernel).
- * eps: host or device [T][2] float64.  cT_dev: device [H][W][C] output c^T (may be NULL).
+ * eps: host or device [T][2] float64, entries finite and >= 0 (the semi-axes of the
+ * ellipsoid; AGENTS_EINVAL otherwise).  cT_dev: device [H][W][C] output c^T (may be NULL).
  * store != 0 keeps the trajectory (or its checkpoints) for a following agents_adjoint. */
 int agents_forward(agents_ctx* ctx, const double* eps, float* cT_dev, int store);
 

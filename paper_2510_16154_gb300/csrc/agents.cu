@@ -362,8 +362,10 @@ int read_control(agents_ctx* ctx, const double* eps, std::vector<double>& host) 
   } else {
     std::memcpy(host.data(), eps, host.size() * sizeof(double));
   }
-  for (double e : host)
+  for (double e : host) {
     if (!std::isfinite(e)) return fail(ctx, AGENTS_EINVAL, "control contains NaN/Inf");
+    if (e < 0.0) return fail(ctx, AGENTS_EINVAL, "control entries must be >= 0 (Eq. ellipsoid)");
+  }
   return AGENTS_OK;
 }
 

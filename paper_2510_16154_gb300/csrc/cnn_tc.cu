@@ -329,6 +329,13 @@ size_t tc_smem_bytes(int nt) { return (size_t)kHeader + 2 * (size_t)stage_bytes(
 
 cudaError_t launch_tc(TcArgs g, int N, cudaStream_t s) {
   const size_t smem = tc_smem_bytes(g.nt);
+  static size_t configured = 0;       // dynamic shared memory the kernel is opted into
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
   // kRows output rows per CTA: each staged weight group serves kRows x 9 MMAs.  (Fewer
   // rows on small grids, for more CTAs, measured slower: 2.70 against 2.36 ms for the
   // network at 1024 x 1024, where the deep layers' weight staging dominates.)

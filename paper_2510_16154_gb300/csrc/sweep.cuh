@@ -11,8 +11,10 @@
 //    registers (16-byte reads) and reuses them for all its pairs (register blocking);
 //  * the arithmetic of a pair runs in packed float2 instructions (sm_100+ FFMA2/FADD2/
 //    FMUL2), halving issued instructions; per lane the operations are the scalar ones;
-//  * the spatial part of r_ij is uniform over pixels, so 1 - r costs one FMA per
-//    interaction from a per-offset constant; phi is branch-free (t = max(1 - r, 0));
+//  * the spatial part of r_ij is uniform over pixels, so it is a per-offset constant; the
+//    forward step stages the colours scaled by sqrt(eps_c / 2), so that r - 1 is the
+//    colour distance's FMA chain started from that constant, and the adjoint forms 1 - r
+//    with one FMA; phi is branch-free (t = max(1 - r, 0));
 //  * interior tiles skip all bounds handling; tiles whose halo leaves the image multiply
 //    each interaction weight by a 0/1 validity plane (exact: out-of-image cells hold 0,
 //    so the weight times a finite difference is exactly 0);
@@ -66,13 +68,13 @@ __device__ __forceinline__ float2 max0(float2 a) {
 }
 
 // Stage NF fields (NHWC, C channels each) of the tile + halo into paired planar shared
-// memory.  Returns true when the halo leaves the image (the validity plane is then
-// filled with 1/0 per cell).
+// memory, field 0 multiplied by s0.  Returns true when the halo leaves the image (the
+// validity plane is then filled with 1/0 per cell).
 template <class T, int R, int C, int NF>
 __device__ __forceinline__ bool load_tile(float2* __restrict__ sm, float2* __restrict__ smask,
                                           const float* __restrict__ f0,
                                           const float* __restrict__ f1, const SweepGeom& g,
-                                          int x0, int y0) {
+                                          int x0, int y0, float s0 = 1.0f) {
   const bool border = (x0 - R < 0) || (y0 - R < 0) || (x0 + T::TW + R > g.W) ||
                       (y0 + T::TH + R > g.H);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -88,8 +90,8 @@ __device__ __forceinline__ bool load_tile(float2* __restrict__ sm, float2* __res
     const size_t bb = okb ? ((size_t)gy * g.W + gb) * C : 0;
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) {
-      sm[ch * T::PLANE + idx] = make_float2(oka ? __ldg(f0 + ba + ch) : 0.0f,
-                                            okb ? __ldg(f0 + bb + ch) : 0.0f);
+      sm[ch * T::PLANE + idx] = make_float2(oka ? s0 * __ldg(f0 + ba + ch) : 0.0f,
+                                            okb ? s0 * __ldg(f0 + bb + ch) : 0.0f);
       if constexpr (NF == 2)
         sm[(C + ch) * T::PLANE + idx] = make_float2(oka ? __ldg(f1 + ba + ch) : 0.0f,
                                                     okb ? __ldg(f1 + bb + ch) : 0.0f);
@@ -124,26 +126,61 @@ __device__ __forceinline__ void store_pairs(float* __restrict__ out, const Sweep
 }
 
 // ------------------------------------------------------------------ forward step
-// Per interaction: delta (C), |delta|^2 (C), 1 - r (one FMA: the spatial part of 1 - r is
-// a per-offset constant), phi = t^4 (5 - 4t) with t = max(1 - r, 0), and C updates; every
-// operation is a packed pair except the clamp.
+// The tile holds the colours scaled by sk = sqrt(eps_c / 2), so that for d = sk (c_j - c_i)
+//   r - 1 = |d|^2 + (eps_x / 2 |x_j - x_i|^2 - 1),
+// one FMA per channel from a per-offset constant; t = max(1 - r, 0), phi = t^4 (5 - 4t),
+// and the update sum_j phi d is taken back to colour units once per pixel
+// (c^{n+1} = c^n + (dt / M) / sk * sum_j phi d, with c^n read unscaled).  Every operation
+// of an interaction is a packed pair except the clamp.
+template <class T, int C, int PXH>
+__device__ __forceinline__ void store_update(float* __restrict__ out,
+                                             const float* __restrict__ src, const SweepGeom& g,
+                                             const float2 (&acc)[PXH][C], float mult, int x0,
+                                             int y0) {
+  const int gy = y0 + threadIdx.y;
+  if (gy >= g.H) return;
+#pragma unroll
+  for (int p = 0; p < PXH; ++p) {
+    const int ga = x0 + threadIdx.x * PXH + p, gb = ga + T::HALF;
+    if (ga < g.W) {
+      const size_t k = ((size_t)gy * g.W + ga) * C;
+#pragma unroll
+      for (int ch = 0; ch < C; ++ch) out[k + ch] = fmaf(mult, acc[p][ch].x, __ldg(src + k + ch));
+    }
+    if (gb < g.W) {
+      const size_t k = ((size_t)gy * g.W + gb) * C;
+#pragma unroll
+      for (int ch = 0; ch < C; ++ch) out[k + ch] = fmaf(mult, acc[p][ch].y, __ldg(src + k + ch));
+    }
+  }
+}
+
+__device__ __forceinline__ float2 max0_neg(float2 a) {
+  return make_float2(fmaxf(-a.x, 0.0f), fmaxf(-a.y, 0.0f));
+}
+
+// Scale of the staged colours: sqrt(eps_c / 2), with eps_c = 0 read as a tiny positive
+// value (its colour term, below 1e-30 |c_j - c_i|^2, is far under float32 resolution).
+__device__ __forceinline__ float colour_scale(float kc) { return sqrtf(fmaxf(kc, 1e-30f)); }
+
 template <class T, int R, int C, int PXH, bool BORDER>
 __device__ __forceinline__ void forward_body(const float2* __restrict__ sm,
                                              const float2* __restrict__ smask,
+                                             const float* __restrict__ src,
                                              float* __restrict__ out, const SweepGeom& g,
-                                             float kx, float ky, float kc, int x0, int y0) {
+                                             float kx, float ky, float mult, int x0, int y0) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int sx = tx * PXH;
-  float2 ci[PXH][C], nci[PXH][C], acc[PXH][C];
+  float2 nci[PXH][C], acc[PXH][C];
 #pragma unroll
   for (int p = 0; p < PXH; ++p)
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) {
-      ci[p][ch] = sm[ch * T::PLANE + (ty + R) * T::SW + sx + R + p];
-      nci[p][ch] = make_float2(-ci[p][ch].x, -ci[p][ch].y);
+      const float2 ci = sm[ch * T::PLANE + (ty + R) * T::SW + sx + R + p];
+      nci[p][ch] = make_float2(-ci.x, -ci.y);
       acc[p][ch] = f2(0.0f);
     }
-  const float2 nkc = f2(-kc), m4 = f2(-4.0f), five = f2(5.0f);
+  const float2 m4 = f2(-4.0f), five = f2(5.0f);
 #pragma unroll 1
   for (int dy = -R; dy <= R; ++dy) {
     const int row = (ty + R + dy) * T::SW + sx;
@@ -152,20 +189,20 @@ __device__ __forceinline__ void forward_body(const float2* __restrict__ sm,
     for (int ch = 0; ch < C; ++ch) load_row<T::SEG>(sm + ch * T::PLANE + row, seg[ch]);
     float2 mseg[BORDER ? T::SEG : 1];
     if constexpr (BORDER) load_row<T::SEG>(smask + row, mseg);
-    const float sy = fmaf(-ky, (float)(dy * dy), 1.0f);
+    const float syn = fmaf(ky, (float)(dy * dy), -1.0f);
 #pragma unroll
     for (int dx = -R; dx <= R; ++dx) {
-      const float2 sp = f2(fmaf(-kx, (float)(dx * dx), sy));   // 1 - spatial part of r
+      const float2 spn = f2(fmaf(kx, (float)(dx * dx), syn));  // spatial part of r, minus 1
 #pragma unroll
       for (int p = 0; p < PXH; ++p) {
         const int e = p + R + dx;
         float2 d[C];
 #pragma unroll
         for (int ch = 0; ch < C; ++ch) d[ch] = __fadd2_rn(seg[ch][e], nci[p][ch]);
-        float2 s2 = __fmul2_rn(d[0], d[0]);
+        float2 u = spn;                                          // r - 1
 #pragma unroll
-        for (int ch = 1; ch < C; ++ch) s2 = __ffma2_rn(d[ch], d[ch], s2);
-        const float2 t = max0(__ffma2_rn(nkc, s2, sp));          // max(1 - r, 0)
+        for (int ch = 0; ch < C; ++ch) u = __ffma2_rn(d[ch], d[ch], u);
+        const float2 t = max0_neg(u);                            // max(1 - r, 0)
         const float2 t2 = __fmul2_rn(t, t);
         float2 ph = __fmul2_rn(__fmul2_rn(t2, t2), __ffma2_rn(m4, t, five));
         if constexpr (BORDER) ph = __fmul2_rn(ph, mseg[e]);
@@ -174,7 +211,7 @@ __device__ __forceinline__ void forward_body(const float2* __restrict__ sm,
       }
     }
   }
-  store_pairs<T, C, PXH>(out, g, ci, acc, x0, y0);
+  store_update<T, C, PXH>(out, src, g, acc, mult, x0, y0);
 }
 
 template <int R, int C, int PXH, int BX, int BY>
@@ -187,12 +224,13 @@ forward_tile_kernel(const float* __restrict__ c, float* __restrict__ out,
   float2* smask = smem2 + C * T::PLANE;
   const int x0 = blockIdx.x * T::TW, y0 = blockIdx.y * T::TH;
   const float ex = (float)eps_n[0], ec = (float)eps_n[1];
-  const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
-  const bool border = load_tile<T, R, C, 1>(sm, smask, c, nullptr, g, x0, y0);
+  const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2;
+  const float sk = colour_scale(0.5f * ec), mult = g.scale / sk;
+  const bool border = load_tile<T, R, C, 1>(sm, smask, c, nullptr, g, x0, y0, sk);
   if (border)
-    forward_body<T, R, C, PXH, true>(sm, smask, out, g, kx, ky, kc, x0, y0);
+    forward_body<T, R, C, PXH, true>(sm, smask, c, out, g, kx, ky, mult, x0, y0);
   else
-    forward_body<T, R, C, PXH, false>(sm, smask, out, g, kx, ky, kc, x0, y0);
+    forward_body<T, R, C, PXH, false>(sm, smask, c, out, g, kx, ky, mult, x0, y0);
 }
 
 // ------------------------------------------------------------------ adjoint step
@@ -362,12 +400,13 @@ forward_batch_kernel(const BatchSweepImg* __restrict__ imgs, const BatchJob* __r
     }
     const int x0 = job.tx * T::TW, y0 = job.ty * T::TH;
     const float ex = (float)eps_n[0], ec = (float)eps_n[1];
-    const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
-    const bool border = load_tile<T, R, C, 1>(sm, smask, src, nullptr, g, x0, y0);
+    const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2;
+    const float sk = colour_scale(0.5f * ec), mult = g.scale / sk;
+    const bool border = load_tile<T, R, C, 1>(sm, smask, src, nullptr, g, x0, y0, sk);
     if (border)
-      forward_body<T, R, C, PXH, true>(sm, smask, dst, g, kx, ky, kc, x0, y0);
+      forward_body<T, R, C, PXH, true>(sm, smask, src, dst, g, kx, ky, mult, x0, y0);
     else
-      forward_body<T, R, C, PXH, false>(sm, smask, dst, g, kx, ky, kc, x0, y0);
+      forward_body<T, R, C, PXH, false>(sm, smask, src, dst, g, kx, ky, mult, x0, y0);
     __syncthreads();  // the next job reuses shared memory
   }
 }

@@ -217,6 +217,9 @@ def test_abi_errors_on_device():
         with pytest.raises(lib.AgentsError) as e:          # NaN control
             lib.agents_forward(ctx.handle, np.full((3, 2), np.nan), None, store=False)
         assert e.value.code == lib.AGENTS_EINVAL
+        with pytest.raises(lib.AgentsError) as e:          # negative semi-axis
+            lib.agents_forward(ctx.handle, np.full((3, 2), -1.0), None, store=False)
+        assert e.value.code == lib.AGENTS_EINVAL
         o = lib.agents_default_solve_opts()
         o.ls_b = 1.5
         with pytest.raises(lib.AgentsError) as e:

@@ -50,6 +50,25 @@ def test_forward_one_step(H, W, C, R):
     assert np.max(np.abs(want - c0)) > 0 or H * W <= 6
 
 
+@pytest.mark.parametrize("ec", [0.0, 1e-6, 1100.0])
+def test_forward_step_colour_weight_extremes(ec):
+    # eps_c = 0 (spatial interaction only), a tiny one and the top of E, on the tiled
+    # kernels (C = 1, 3) and the wide one (C = 31)
+    ensure_lib()
+    for H, W, C, R in [(40, 70, 3, 5), (23, 67, 1, 2), (20, 40, 31, 3)]:
+        rng = np.random.default_rng(H + W + C)
+        c0 = _field(rng, H, W, C)
+        p, op = params(H, W, C, R, 1, eps_lo=(0.0, 0.0))
+        eps = np.array([[30.0, ec]])
+        with lib.Context(p, dev(c0, np.float32)) as ctx:
+            out = zeros_dev(H, W, C)
+            lib.agents_forward(ctx.handle, eps, out, store=False)
+            got = host(out).astype(np.float64)
+        want = oracle.forward_final(c0, eps, op)
+        assert np.max(np.abs(got - want)) <= 1e-6
+        assert np.max(np.abs(want - c0)) > 0 or ec > 100   # large eps_c: colours apart
+
+
 @pytest.mark.parametrize("norm_mode", [0, 1])
 def test_forward_sweep_20_steps(norm_mode):
     ensure_lib()
