@@ -13,6 +13,7 @@
 // block then reduces in float64 with a fixed shuffle tree, writing one partial per block;
 // launch_reduce_rows adds the partials in a fixed order (bitwise reproducible).
 #include "common.cuh"
+#include "fp_bits.cuh"
 #include "kernels.h"
 
 namespace agents {
@@ -43,20 +44,20 @@ __device__ __forceinline__ float grad_y(const float* __restrict__ c, const TvGeo
   return (__ldg(c + (k + g.W) * C + ch) - __ldg(c + (k - g.W) * C + ch)) * g.inv2hy;
 }
 
-// (G c) in float64 (the differences of float32 values are exact in float64).
+// (G c) in float64 (the differences of float32 values are exact in float64).  The
+// operands are widened with integer operations (widen, fp_bits.cuh): the float64 pipe
+// is left to the arithmetic.
 __device__ __forceinline__ double grad_x_f64(const float* __restrict__ c, const TvGeom& g, int r,
-                                             int q, int C, int ch) {
+                                             int q, int C, int ch, double inv2hx) {
   if (q < 1 || q > g.W - 2) return 0.0;
   const size_t k = (size_t)r * g.W + q;
-  return ((double)__ldg(c + (k + 1) * C + ch) - (double)__ldg(c + (k - 1) * C + ch)) *
-         (double)g.inv2hx;
+  return (widen(__ldg(c + (k + 1) * C + ch)) - widen(__ldg(c + (k - 1) * C + ch))) * inv2hx;
 }
 __device__ __forceinline__ double grad_y_f64(const float* __restrict__ c, const TvGeom& g, int r,
-                                             int q, int C, int ch) {
+                                             int q, int C, int ch, double inv2hy) {
   if (r < 1 || r > g.H - 2) return 0.0;
   const size_t k = (size_t)r * g.W + q;
-  return ((double)__ldg(c + (k + g.W) * C + ch) - (double)__ldg(c + (k - g.W) * C + ch)) *
-         (double)g.inv2hy;
+  return (widen(__ldg(c + (k + g.W) * C + ch)) - widen(__ldg(c + (k - g.W) * C + ch))) * inv2hy;
 }
 
 // ------------------------------------------------------------------ objective / terminal
@@ -343,7 +344,8 @@ cudaError_t launch_pd_tv_step(const float* c, const float* mu, float* v, const T
 
 // ------------------------------------------------------------------ multiplier update
 // mu <- mu + gamma (v - G c), evaluated in float64 (G c included) and rounded once to
-// float32.
+// float32; the conversions between the two formats are the integer ones of fp_bits.cuh
+// (exact widening, round-to-nearest-even narrowing: bitwise those of the hardware).
 // Per-block partial sums: |v - Gc|^2, |G^T (v - v_prev)|^2, |c - c_prev|^2, |c|^2 and
 // K(c)/(dx dy) = sum |G c_i| + alpha/2 |c_i - c0_i|^2.
 template <int CT>
@@ -357,7 +359,7 @@ __device__ __forceinline__ void alm_block(int bx, int by, const float* __restric
   const int C = nch<CT>(g);
   const int r = by * kTvBY + threadIdx.y;
   float a_r2 = 0.0f, a_s2 = 0.0f, a_dc2 = 0.0f, a_cn2 = 0.0f, a_K = 0.0f;
-  const double gam = g.gamma;
+  const double gam = g.gamma, inv2hx = (double)g.inv2hx, inv2hy = (double)g.inv2hy;
   if (r < g.H) {
 #pragma unroll
     for (int i = 0; i < kPPT; ++i) {
@@ -368,13 +370,14 @@ __device__ __forceinline__ void alm_block(int bx, int by, const float* __restric
       float* mk = mu + k * 2 * C;
       float gg2 = 0.0f, tvs = 0.0f, fid = 0.0f;
       for (int ch = 0; ch < C; ++ch) {
-        const double gxd = grad_x_f64(c, g, r, q, C, ch), gyd = grad_y_f64(c, g, r, q, C, ch);
+        const double gxd = grad_x_f64(c, g, r, q, C, ch, inv2hx);
+        const double gyd = grad_y_f64(c, g, r, q, C, ch, inv2hy);
         const float vx = __ldg(vk + ch), vy = __ldg(vk + C + ch);
-        const double dxd = (double)vx - gxd, dyd = (double)vy - gyd;
-        mk[ch] = (float)fma(gam, dxd, (double)mk[ch]);
-        mk[C + ch] = (float)fma(gam, dyd, (double)mk[C + ch]);
-        const float gx = (float)gxd, gy = (float)gyd;
-        const float rx = (float)dxd, ry = (float)dyd;
+        const double dxd = widen(vx) - gxd, dyd = widen(vy) - gyd;
+        mk[ch] = narrow(fma(gam, dxd, widen(mk[ch])));
+        mk[C + ch] = narrow(fma(gam, dyd, widen(mk[C + ch])));
+        const float gx = narrow(gxd), gy = narrow(gyd);
+        const float rx = narrow(dxd), ry = narrow(dyd);
         a_r2 = fmaf(rx, rx, fmaf(ry, ry, a_r2));
         if (g.tv_mode == 0) gg2 = fmaf(gx, gx, fmaf(gy, gy, gg2));
         else tvs += sqrtf(fmaf(gx, gx, gy * gy));
