@@ -715,14 +715,15 @@ def main():
     peaks = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(sm_max)
-    # DRAM traffic of this kernel from ncu at 4096 x 4096 x 3 (fields larger than L2; see
-    # profiles/forward_tile_kernel_4096x4096x3_R5.md): 201.35 MB read + 158.56 MB written
-    # per launch, scaled by pixels to this launch; at 1024^2 the fields fit in L2, so the
-    # launch's own DRAM traffic is at most this.
-    traffic = (201.348864e6 + 158.556416e6) * (H * W) / (4096 * 4096)
+    # DRAM traffic: the ncu capture at 4096 x 4096 x 3 (201.35 MB read + 158.56 MB written
+    # per launch, profiles/forward_tile_kernel_4096x4096x3_R5.md) predates the kernel's
+    # pre-scaled colour tile and its re-read of the unscaled centre values at the store,
+    # so it no longer describes this kernel and is not reported.
+    traffic = None
     roofline = {"bound": "alu", "kernel": "forward_tile_kernel<5,3>", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_basis": "ncu dram bytes at 4096x4096x3 scaled by pixels",
+                "traffic_basis": "none: the kernel changed after its ncu capture (201.35 MB read "
+                                 "+ 158.56 MB written per 4096x4096x3 launch before)",
                 "algorithmic_bytes": 8 * C * H * W,
                 "peak_basis": f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (max SM clock)",
                 "launch_us": launch_s * 1e6,
