@@ -152,6 +152,37 @@ def test_control_derivative_by_finite_differences(rng):
     assert D[1] == pytest.approx(fc, rel=1e-6, abs=1e-12)
 
 
+@pytest.mark.parametrize("H,W,C,R", [(9, 13, 3, 3), (5, 6, 1, 6), (7, 4, 2, 1)])
+def test_control_derivative_paired_form(H, W, C, R, rng):
+    # D_x = 1/(2M) sum_i sum_j phi'(r_ij) |x_j - x_i|^2 (lam_i . delta_ij) (likewise D_c
+    # with |delta_ij|^2).  phi'(r_ij) and both distances are symmetric in (i, j), delta_ij
+    # is antisymmetric and the window relation is symmetric, so pairing (i, j) with
+    # (j, i) gives -1/2 sum_i sum_j phi'(r_ij) |x_j - x_i|^2 (delta_ij . (lam_j - lam_i)):
+    # the form the GPU adjoint accumulates.  Brute force over ordered pairs.
+    c = rng.uniform(0.3, 0.7, size=(H, W, C))
+    lam = rng.normal(size=c.shape)
+    p = Params(radius=R)
+    ex, ec = 37.0, 11.0
+    M = (2 * R + 1) ** 2
+    paired = np.zeros(2)
+    for i in range(H):
+        for j in range(W):
+            for k in range(max(0, i - R), min(H, i + R + 1)):
+                for m in range(max(0, j - R), min(W, j + R + 1)):
+                    if (k, m) == (i, j):
+                        continue
+                    d = c[k, m] - c[i, j]
+                    s = float(d @ d)
+                    d2 = ((m - j) / W) ** 2 + ((k - i) / H) ** 2
+                    r = 0.5 * ex * d2 + 0.5 * ec * s
+                    g = float(dphi(r)) * float(d @ (lam[k, m] - lam[i, j]))
+                    paired += -0.5 * g * np.array([d2, s])
+    paired /= 2 * M
+    D = control_derivative(c, lam, ex, ec, p)
+    assert np.all(np.abs(paired) > 1e-7)
+    assert np.allclose(D, paired, rtol=1e-12, atol=1e-18)
+
+
 def _adjoint_case(rng, C=3, H=8, W=8, T=6):
     img = rng.uniform(0.2, 0.8, size=(H, W, C))
     p = Params(radius=2, nsteps=T, alpha=30.0, rho=0.5)
