@@ -185,3 +185,54 @@ def test_rof_two_level_step_chambolle_pock():
     assert gaps[-1] <= 1e-6 * gaps[0]
     run = np.minimum.accumulate(gaps)
     assert np.all(np.diff(run) <= 0.0)
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_alm_stats_hand_example(axis):
+    # three pixels along one axis, C = 1, spacing h = 1/3: 1/(2h) = 1.5.  Only the middle
+    # pixel has a central difference; (G c)_mid = 1.5 (c_2 - c_0) and G^T w sends the
+    # middle pixel's w to (-1.5 w, 0, +1.5 w).
+    shape = (1, 3, 1) if axis == "x" else (3, 1, 1)
+    comp = 0 if axis == "x" else 1
+    c = np.array([1.0, 2.0, 2.0]).reshape(shape)
+    c_prev = np.array([1.0, 2.0, 0.0]).reshape(shape)
+    c0 = np.zeros(shape)
+    v = np.zeros(shape[:2] + (2, 1))
+    v_prev = np.zeros_like(v)
+    mid = (0, 1) if axis == "x" else (1, 0)
+    v[mid + (comp, 0)] = 5.0
+    v_prev[mid + (comp, 0)] = 3.0
+    p = Params(alpha=4.0, rho=0.37, gamma=0.21)
+    st = alm_stats(c, v, v_prev, c_prev, c0, p)
+    # v - G c = 5 - 1.5 = 3.5 at the middle pixel, 0 elsewhere
+    assert st["r"] == pytest.approx(3.5, rel=1e-15)
+    assert st["gap"] == pytest.approx(0.21 * (1.0 / 3.0) * 3.5 ** 2, rel=1e-14)
+    # G^T (v - v_prev) = (-3, 0, 3): s = rho * 3 sqrt(2)
+    assert st["s"] == pytest.approx(0.37 * 3.0 * np.sqrt(2.0), rel=1e-14)
+    # |c - c_prev| = 2, |c| = 3
+    assert st["rel_dc"] == pytest.approx(2.0 / 3.0, rel=1e-15)
+    # K = dx dy [|G c| + alpha/2 |c - c0|^2] = (1/3)(1.5 + 2 * 9)
+    assert st["K"] == pytest.approx((1.0 / 3.0) * (1.5 + 2.0 * 9.0), rel=1e-14)
+
+
+def test_alm_stats_dual_residual_against_dense_transpose(rng):
+    # s = rho |G^T (v - v_prev)| with G^T the transpose of a dense G assembled column by
+    # column from unit images; rel_dc from its definition on random fields
+    H, W, C = 4, 5, 2
+    N = H * W
+    dense = np.zeros((2 * N * C, N * C))
+    for k in range(N * C):
+        e = np.zeros(N * C)
+        e[k] = 1.0
+        dense[:, k] = grad(e.reshape(H, W, C)).reshape(-1)
+    c0, c, v, _ = _fields(rng, H, W, C)
+    c_prev = c + rng.normal(scale=0.05, size=c.shape)
+    v_prev = v + rng.normal(scale=0.5, size=v.shape)
+    p = Params(alpha=7.0, rho=0.37, gamma=0.21)
+    st = alm_stats(c, v, v_prev, c_prev, c0, p)
+    s_dense = 0.37 * np.linalg.norm(dense.T @ (v - v_prev).reshape(-1))
+    assert st["s"] == pytest.approx(s_dense, rel=1e-12)
+    rel = np.sqrt(np.sum((c - c_prev) ** 2)) / np.sqrt(np.sum(c * c))
+    assert st["rel_dc"] == pytest.approx(rel, rel=1e-13)
+    r_dense = np.linalg.norm(v.reshape(-1) - dense @ c.reshape(-1))
+    assert st["r"] == pytest.approx(r_dense, rel=1e-13)
