@@ -74,9 +74,51 @@ def adjoint_flops_per_launch(h, w, c, r):
     return pairs2 / 2 * (11 * c + 18)
 
 
-def fp32_peak_tflops(sm_mhz: float) -> float:
-    """152 SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_derived_tflops(sms: int, sm_mhz: float) -> float:
+    """Unit-count figure for context: SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measure_fp32_peak(torch, lib, dev, seconds: float = 0.6):
+    """Measured FP32 rate: the library's FMA probe (independent FFMA / FFMA2 chains, no
+    memory traffic; 8 blocks of 256 threads per SM) timed with CUDA events on its own
+    stream, best launch of each form, SM clocks sampled meanwhile.  The larger of the two
+    forms is the denominator of the agent sweeps' roofline fractions."""
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    blocks = sms * 8
+    sink = torch.zeros(blocks * 256, dtype=torch.float32, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = str(props.uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    out = {"sms": sms, "blocks": blocks, "threads_per_block": 256}
+    sampler.start()
+    for packed in (False, True):
+        iters = 20000
+        lib.agents_fp32_probe(packed, blocks, iters, sink, s)        # warm
+        torch.cuda.synchronize()
+        best = 0.0
+        deadline = time.perf_counter() + seconds / 2
+        while time.perf_counter() < deadline or best == 0.0:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            flops = lib.agents_fp32_probe(packed, blocks, iters, sink, s)
+            e1.record(s)
+            e1.synchronize()
+            best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        out["ffma2_tflops" if packed else "ffma_tflops"] = best
+    clocks = sampler.stop()
+    out["tflops"] = max(out["ffma_tflops"], out["ffma2_tflops"])
+    out["clocks"] = clocks
+    mhz = (clocks or {}).get("sm_mhz") or 0.0
+    if mhz:
+        out["derived_tflops_at_clock"] = fp32_derived_tflops(sms, mhz)
+    return out
 
 
 def load_peaks():
@@ -143,7 +185,8 @@ FP64_FLOPS_PER_PIXEL_ALM = 10   # per channel: 2 gradients (sub, mul each), 2 re
 
 
 def measure_kernels(torch, lib, dev, stream, size: int, reps: int = 5, only: str | None = None,
-                    channels: int = 3, radius: int = R):
+                    channels: int = 3, radius: int = R, alu_peak: float | None = None,
+                    alu_basis: str = ""):
     """Average device time of each kernel on a size x size x channels image with window
     radius `radius` (default 3 channels, R = 5), with CUDA events on the library's
     stream.  Fields of 4096^2 x 3 float32 (201 MB) exceed the 129 MB L2, so the HBM-bound
@@ -199,14 +242,17 @@ def measure_kernels(torch, lib, dev, stream, size: int, reps: int = 5, only: str
                               "note": "per step; the terminal adjoint of the sweep subtracted"}
     peaks = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if alu_peak is None:
+        fp = measure_fp32_peak(torch, lib, dev, seconds=0.3)
+        alu_peak = fp["tflops"]
+        alu_basis = "measured FMA probe"
     for name, rec in out.items():
         t = rec["us"] / 1e6
         if name in ("forward", "adjoint"):
             fl = (forward_flops_per_launch if name == "forward" else adjoint_flops_per_launch)(
                 Hs, Ws, Cs, radius)
             rec.update({"bound": "alu", "achieved": fl / t / 1e12, "unit": "TFLOP/s",
-                        "peak": fp32_peak_tflops(sm_max)})
+                        "peak": alu_peak, "peak_basis": alu_basis, "flops": fl})
         elif name == "alm_update":
             by = BYTES_PER_PIXEL[name](Cs) * Hs * Ws
             fl = FP64_FLOPS_PER_PIXEL_ALM * Cs * Hs * Ws
@@ -609,6 +655,11 @@ def main():
         dist.barrier()
     lib.load()
     stream = torch.cuda.Stream(device=dev)
+    if args.kernel == "fp32_probe":
+        res = measure_fp32_peak(torch, lib, dev, seconds=2.0)
+        if rank == 0:
+            print(json.dumps({"kernel": args.kernel, **res}), flush=True)
+        return 0
     if args.workload == "gradient":
         res = gradient_workload(torch, lib, dev)
         if rank == 0:
@@ -712,9 +763,12 @@ def main():
     launch_s = e0.elapsed_time(e1) / 1e3 / (reps * T)
     flops = forward_flops_per_launch(H, W, C, R)
     achieved = flops / launch_s / 1e12
-    peaks = load_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = fp32_peak_tflops(sm_max)
+    fp32 = measure_fp32_peak(torch, lib, dev)
+    peak = fp32["tflops"]
+    fp32_clock = (fp32.get("clocks") or {}).get("sm_mhz")
+    peak_basis = (f"measured: FMA probe ({'FFMA2' if fp32['ffma2_tflops'] >= fp32['ffma_tflops'] else 'FFMA'}"
+                  f" chains, {fp32['sms']} SMs x 8 blocks x 256 threads) at a median "
+                  f"{fp32_clock} MHz SM clock")
     # DRAM traffic: the ncu capture at 4096 x 4096 x 3 (201.35 MB read + 158.56 MB written
     # per launch, profiles/forward_tile_kernel_4096x4096x3_R5.md) predates the kernel's
     # pre-scaled colour tile and its re-read of the unscaled centre values at the store,
@@ -725,7 +779,7 @@ def main():
                 "traffic_basis": "none: the kernel changed after its ncu capture (201.35 MB read "
                                  "+ 158.56 MB written per 4096x4096x3 launch before)",
                 "algorithmic_bytes": 8 * C * H * W,
-                "peak_basis": f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (max SM clock)",
+                "peak_basis": peak_basis, "fp32_probe": fp32,
                 "launch_us": launch_s * 1e6,
                 "flops_per_launch": flops}
 
@@ -757,7 +811,8 @@ def main():
     kernels = None
     if args.kernel_size > 0:
         kernels = {"size": f"{args.kernel_size}x{args.kernel_size}x3, R={R}",
-                   **measure_kernels(torch, lib, dev, stream, args.kernel_size)}
+                   **measure_kernels(torch, lib, dev, stream, args.kernel_size,
+                                     alu_peak=peak, alu_basis="measured FMA probe")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

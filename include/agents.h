@@ -85,6 +85,29 @@ int agents_set_image(agents_ctx* ctx, const float* c0);
 /* Release every device buffer of the context.  NULL is accepted. */
 int agents_destroy(agents_ctx* ctx);
 
+/* Process-wide cap, in bytes, on the device memory that this library's contexts hold
+ * (their workspaces, trajectories and solve buffers, across every context and device of
+ * the process); 0 removes the cap, which is the default.  The paper has no counterpart:
+ * this lets a service bound what the solver may take from a shared GPU.  An allocation
+ * that would take the total above the cap fails as a failed cudaMalloc does:
+ * agents_init (or the first solve, dal_solve or agents_solve_batch on a context, which
+ * allocate the solve buffers) returns AGENTS_ENOMEM and agents_last_error names the
+ * limit; the optional trajectory-reuse buffers of solve() are skipped instead (solve
+ * then recomputes, with bitwise the same results).  Memory already held is not released
+ * by lowering the cap.  Always returns AGENTS_OK. */
+int agents_set_memory_limit(uint64_t bytes);
+
+/* Device memory, in bytes, currently held by all contexts of the process. */
+uint64_t agents_memory_held(void);
+
+/* Test hook (no counterpart in the paper): bound every loop of the label union-find of
+ * agents_labels and solve() at `cap` iterations instead of the pixel count (0 restores
+ * the default; cap < 0 returns AGENTS_EINVAL).  With a bound below the tree depth the
+ * loops give up -- they exit, nothing hangs or reads out of bounds -- and the call
+ * returns AGENTS_ETIMEOUT, the status of a device-side wait that gave up.  Process-wide;
+ * not for production use. */
+int agents_debug_set_label_loop_cap(int32_t cap);
+
 /* Message of the last failure on ctx (or of the last failed agents_init when ctx is
  * NULL).  The string is owned by the library and valid until the next call. */
 const char* agents_last_error(const agents_ctx* ctx);
@@ -122,6 +145,17 @@ int agents_adjoint(agents_ctx* ctx, const double* eps, const float* v_dev, const
  * forward sweep. */
 int agents_adjoint_from(agents_ctx* ctx, const double* eps, const float* lambdaT_dev,
                         double* D_out, float* lambda0_dev);
+
+/* Backward pass of the differentiable forward sweep c^T = c(T; eps, c^0) for any
+ * terminal cost L(c^T): given the upstream gradient grad_cT_dev = dL/dc^T (device
+ * [H][W][C]) it runs the exact discrete adjoint (Eq. opt_system-b, Section 3.1) from
+ * lambda^T = -dL/dc^T and writes grad_eps_out = dL/deps^n = -dt D^n (host or device
+ * [T][2] float64, may be NULL) and grad_c0_dev = dL/dc^0 = -lambda^0 (device [H][W][C],
+ * may be NULL).  The sign changes and the dt scaling run on the device.  Requires a
+ * preceding agents_forward(store != 0) with the same eps (else AGENTS_ESTATE); full
+ * storage or checkpoints (traj_mode). */
+int agents_flow_backward(agents_ctx* ctx, const double* eps, const float* grad_cT_dev,
+                         double* grad_eps_out, float* grad_c0_dev);
 
 /* Terminal cost and adjoint only: obj_out (host or device) = L~(c, v, mu) of
  * Eq. complete_square; lambda_dev (device, may be NULL) = -dL~/dc (Eq. admm_terminal,
@@ -290,23 +324,45 @@ int solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float*
  * the caller, and its only scratch, the float64 per-block partial sums of the reduction,
  * lives in a 256 KiB static device array that every GPU loading the library holds until
  * the process exits.  It calls no cudaMalloc, cudaFree or allocating library routine.
- *   obj_dev (device, one float64) = L~(c, v, mu) of Eq. complete_square;
- *   lambda_dev (device [H][W][C], may be NULL) = -dL~/dc (exact-transpose form);
- *   c_dev, c0_dev: device [H][W][C]; v_dev, mu_dev: device [H][W][2][C], 16-byte aligned;
+ *   obj_dev (device, one float64) = the same objective value agents_objective returns:
+ *     the complete-square penalty of v - G c + mu/rho, plus the TV norm of v, plus the
+ *     fidelity term alpha/2 |c - c0|^2, summed over pixels and scaled by dx dy;
+ *   lambda_dev (device [H][W][C], may be NULL) = minus its derivative in c, the terminal
+ *     adjoint agents_objective writes;
+ *   c_dev, c0_dev: device [H][W][C]; v_dev, mu_dev: device [H][W][2][C]; every field is
+ *     device memory, 16-byte aligned, and holds at least that many floats (the library
+ *     cannot check sizes: a short buffer is read out of bounds);
  *   alpha, rho > 0; tv_mode as in agents_params; cuda_stream as in agents_init.
- * Limit: images of at most 33,554,432 pixels (32768 reduction blocks of 128 x 8 pixels);
- * larger images and bad arguments return AGENTS_EINVAL with a message in
- * agents_last_error(NULL).  The first call on each device (with that device current)
- * looks up the array's device address and caches it; make that first call before any
- * stream capture.  All calls share the array, so calls whose work overlaps on the GPU
- * (different streams, no ordering between them) race and must not be issued; calls on
- * one stream are ordered and safe.  Nothing in the array needs clearing between calls:
- * each call writes every partial it reads.  Returns after queueing the work
- * (stream-ordered). */
+ * Limit: ceil(W / 128) * ceil(H / 8) <= 32768 reduction blocks (each block covers
+ * 128 x 8 pixels), e.g. 4096 x 8192; the pixel count 33,554,432 is reached only when W
+ * is a multiple of 128 and H a multiple of 8, and narrow images reach the block limit at
+ * fewer pixels.  Larger images, host pointers and other bad arguments return
+ * AGENTS_EINVAL with a message in agents_last_error(NULL).
+ * Set-up: the first call on each device (with that device current) loads the library's
+ * device code there, which allocates the static array and can synchronise the device;
+ * make that first call during set-up, before any stream capture.  Every call looks up the
+ * array's address in the current device context (no address is cached across calls, so
+ * a device reset or another context of the same device is handled).
+ * All calls share the array, so calls whose work overlaps on the GPU (different streams,
+ * no ordering between them) race and must not be issued; calls on one stream are ordered
+ * and safe.  Nothing in the array needs clearing between calls: each call writes every
+ * partial it reads.  Returns after queueing the work (stream-ordered). */
 int agents_objective_noalloc(int32_t height, int32_t width, int32_t channels, double alpha,
                              double rho, int32_t tv_mode, const float* c_dev,
                              const float* c0_dev, const float* v_dev, const float* mu_dev,
                              double* obj_dev, float* lambda_dev, void* cuda_stream);
+
+/* Measurement utility (no counterpart in the paper): launch one kernel of independent
+ * float32 FMA chains on cuda_stream -- scalar FFMA (packed = 0) or packed FFMA2 on float2
+ * (packed != 0) -- with `blocks` blocks of 256 threads, each thread doing `iters`
+ * iterations of 16 FMAs, no memory traffic.  *flops_out (host) receives the flop count
+ * of the launch (an FMA counts 2).  Timed with events on that stream, it gives the
+ * measured FP32 rate that the agent sweeps' roofline fractions are taken against.
+ * sink_dev: device memory of blocks * 256 floats (written only in a case that never
+ * occurs; it keeps the chains live).  AGENTS_EINVAL on a bad argument, AGENTS_ECUDA if
+ * the launch fails. */
+int agents_fp32_probe(int32_t packed, int32_t blocks, int32_t iters, float* sink_dev,
+                      void* cuda_stream, double* flops_out);
 
 #ifdef __cplusplus
 }

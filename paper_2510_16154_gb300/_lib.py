@@ -84,11 +84,17 @@ _SIGNATURES = {
     "agents_init": (c_int, [POINTER(agents_params), c_void_p, c_void_p, POINTER(c_void_p)]),
     "agents_set_image": (c_int, [c_void_p, c_void_p]),
     "agents_destroy": (c_int, [c_void_p]),
+    "agents_set_memory_limit": (c_int, [ctypes.c_uint64]),
+    "agents_memory_held": (ctypes.c_uint64, []),
+    "agents_debug_set_label_loop_cap": (c_int, [c_int32]),
+    "agents_fp32_probe": (c_int, [c_int32, c_int32, c_int32, c_void_p, c_void_p,
+                                  POINTER(c_double)]),
     "agents_last_error": (ctypes.c_char_p, [c_void_p]),
     "agents_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "agents_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "agents_objective": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "agents_adjoint_from": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "agents_flow_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pd_tv_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "alm_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "agents_labels": (c_int, [c_void_p, c_void_p, c_float, c_void_p, c_void_p]),
@@ -213,6 +219,27 @@ def agents_destroy(ctx):
     _check(load().agents_destroy(ctx), "agents_destroy")
 
 
+def agents_set_memory_limit(nbytes: int):
+    _check(load().agents_set_memory_limit(int(nbytes)), "agents_set_memory_limit")
+
+
+def agents_memory_held() -> int:
+    return int(load().agents_memory_held())
+
+
+def agents_debug_set_label_loop_cap(cap: int):
+    _check(load().agents_debug_set_label_loop_cap(int(cap)), "agents_debug_set_label_loop_cap")
+
+
+def agents_fp32_probe(packed: bool, blocks: int, iters: int, sink, stream=None) -> float:
+    """Launch the FP32 FMA probe kernel; returns its flop count."""
+    flops = c_double(0.0)
+    _check(load().agents_fp32_probe(int(bool(packed)), int(blocks), int(iters),
+                                    _ptr(sink, "float32"), _stream(stream),
+                                    ctypes.byref(flops)), "agents_fp32_probe")
+    return flops.value
+
+
 def agents_last_error(ctx=None) -> str:
     msg = load().agents_last_error(ctx)
     return msg.decode() if msg else ""
@@ -234,6 +261,12 @@ def agents_adjoint_from(ctx, eps, lambdaT, D_out, lambda0=None):
     _check(load().agents_adjoint_from(ctx, _ptr(eps, "float64"), _ptr(lambdaT, "float32"),
                                       _ptr(D_out, "float64"), _ptr(lambda0, "float32")),
            "agents_adjoint_from", ctx)
+
+
+def agents_flow_backward(ctx, eps, grad_cT, grad_eps=None, grad_c0=None):
+    _check(load().agents_flow_backward(ctx, _ptr(eps, "float64"), _ptr(grad_cT, "float32"),
+                                       _ptr(grad_eps, "float64"), _ptr(grad_c0, "float32")),
+           "agents_flow_backward", ctx)
 
 
 def agents_objective(ctx, c, v, mu, obj_out=None, lam=None):
@@ -288,9 +321,14 @@ def agents_solve_batch(ctxs, opts: agents_solve_opts, eps_list, mu_list, c_out_l
     if c_out_list is not None:
         outs = (c_void_p * n)(*[_ptr(c, "float32") for c in c_out_list])
     infos = (agents_solve_info * n)()
-    _check(load().agents_solve_batch(n, arr, ctypes.byref(opts), int(bool(autotune)),
-                                     int(bool(use_graph)), eps, mus, outs, infos),
-           "agents_solve_batch", ctxs[0])
+    st = load().agents_solve_batch(n, arr, ctypes.byref(opts), int(bool(autotune)),
+                                   int(bool(use_graph)), eps, mus, outs, infos)
+    try:
+        _check(st, "agents_solve_batch", ctxs[0])
+    except AgentsError as err:
+        # AGENTS_EDIVERGED still writes every image's outputs and record
+        err.infos = list(infos) if st == AGENTS_EDIVERGED else None
+        raise
     return list(infos)
 
 
@@ -329,10 +367,27 @@ def write_solve_log_jsonl(ctx, path, info=None):
             f.write(json.dumps({"kind": "info", **info.as_dict()}) + "\n")
 
 
+def _require_cuda(name, x, numel, dtype):
+    if not (hasattr(x, "is_cuda") and x.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if str(x.dtype).split(".")[-1] != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {x.dtype}")
+    if x.numel() < numel:
+        raise ValueError(f"{name} holds {x.numel()} elements, needs at least {numel}")
+
+
 def agents_objective_noalloc(height, width, channels, alpha, rho, tv_mode, c, c0, v, mu,
                              obj_out, lam=None, stream=None):
     """Objective and terminal adjoint with no device allocation (caller-owned inputs and
-    outputs, a static device scratch array inside the library)."""
+    outputs, a static device scratch array inside the library).  Every buffer must be a
+    CUDA tensor holding at least its field's element count: the library cannot check
+    sizes."""
+    n = int(height) * int(width) * int(channels)
+    for name, x, k in (("c", c, n), ("c0", c0, n), ("v", v, 2 * n), ("mu", mu, 2 * n)):
+        _require_cuda(name, x, k, "float32")
+    _require_cuda("obj_out", obj_out, 1, "float64")
+    if lam is not None:
+        _require_cuda("lam", lam, n, "float32")
     _check(load().agents_objective_noalloc(height, width, channels, alpha, rho, tv_mode,
                                            _ptr(c, "float32"), _ptr(c0, "float32"),
                                            _ptr(v, "float32"), _ptr(mu, "float32"),

@@ -2,9 +2,10 @@
 
 ``flow(context, eps, c0)`` returns the final colour field c(T; eps, c0) of the agent
 dynamics (Eq. MAsystem, explicit Euler); its backward pass is the library's exact
-discrete adjoint (``agents_adjoint_from``): for an upstream gradient g = dL/dc(T) it
+discrete adjoint (``agents_flow_backward``): for an upstream gradient g = dL/dc(T) it
 runs the reverse sweep from lambda(T) = -g and returns dL/deps^n = -dt D^n and
-dL/dc0 = -lambda(0) (Section 3.1: the adjoint of Eq. opt_system-b).  Long horizons use
+dL/dc0 = -lambda(0) (Section 3.1: the adjoint of Eq. opt_system-b), the sign changes and
+the dt scaling done on the device.  Long horizons use
 the context's checkpointing (``traj_mode = k``: every k-th state is kept and the others
 are recomputed segment by segment during the backward pass, k ~ sqrt(T)).
 
@@ -62,12 +63,11 @@ class AgentsFlow(torch.autograd.Function):
             raise RuntimeError("the context ran another stored forward sweep since this one; "
                                "its trajectory is gone")
         (eps,) = fctx.saved_tensors
-        lamT = (-grad_cT).to(torch.float32).contiguous()
-        D = torch.empty(eps.shape, dtype=torch.float64, device=lamT.device)
-        lam0 = torch.empty_like(lamT) if fctx.needs_input_grad[1] else None
-        lib.agents_adjoint_from(context.handle, eps, lamT, D, lam0)
-        grad_eps = (-context.params.dt * D).to(eps.device) if fctx.needs_input_grad[0] else None
-        grad_c0 = -lam0 if lam0 is not None else None
+        g = grad_cT.to(torch.float32).contiguous()
+        grad_eps = torch.empty(eps.shape, dtype=torch.float64, device=eps.device) \
+            if fctx.needs_input_grad[0] else None
+        grad_c0 = torch.empty_like(g) if fctx.needs_input_grad[1] else None
+        lib.agents_flow_backward(context.handle, eps, g, grad_eps, grad_c0)
         return grad_eps, grad_c0, None
 
 

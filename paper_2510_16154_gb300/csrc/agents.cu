@@ -11,6 +11,7 @@
 #include "kernels.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -52,7 +53,68 @@ bool is_device_ptr(const void* p) {
 namespace agents {
 // Message returned by agents_last_error(NULL) for calls that have no context.
 void set_global_error(const std::string& msg) { g_init_error = msg; }
+
+// Process-wide accounting of the device memory held by contexts, against an optional
+// cap (agents_set_memory_limit; 0 = no cap).
+namespace {
+std::atomic<uint64_t> g_mem_limit{0};
+std::atomic<uint64_t> g_mem_held{0};
+std::atomic<int32_t> g_label_loop_cap{0};
+}  // namespace
+
+bool mem_reserve(size_t bytes) {
+  uint64_t held = g_mem_held.load();
+  for (;;) {
+    const uint64_t lim = g_mem_limit.load();
+    if (lim != 0 && (held > lim || bytes > lim - held)) return false;
+    if (g_mem_held.compare_exchange_weak(held, held + bytes)) return true;
+  }
+}
+
+void mem_release(size_t bytes) { g_mem_held.fetch_sub(bytes); }
+
+// cudaMalloc of a context-owned buffer, counted against the limit.  Returns AGENTS_OK,
+// or AGENTS_ENOMEM (limit reached or cudaMalloc failed) with the message in ctx->err.
+int ctx_alloc(agents_ctx* ctx, void** out, size_t bytes) {
+  if (bytes == 0) bytes = 1;
+  if (!mem_reserve(bytes))
+    return ctx_fail(ctx, AGENTS_ENOMEM,
+                    ("allocation of " + std::to_string(bytes) + " bytes exceeds the memory "
+                     "limit of " + std::to_string(g_mem_limit.load()) + " bytes (" +
+                     std::to_string(g_mem_held.load()) + " held)").c_str());
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    mem_release(bytes);
+    return ctx_fail(ctx, AGENTS_ENOMEM,
+                    ("cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                     cudaGetErrorString(e)).c_str());
+  }
+  ctx->allocs.push_back(p);
+  ctx->held_bytes += bytes;
+  *out = p;
+  return AGENTS_OK;
+}
+
+int32_t label_loop_cap() { return g_label_loop_cap.load(); }
 }  // namespace agents
+
+int agents_set_memory_limit(uint64_t bytes) {
+  agents::g_mem_limit.store(bytes);
+  return AGENTS_OK;
+}
+
+uint64_t agents_memory_held(void) { return agents::g_mem_held.load(); }
+
+int agents_debug_set_label_loop_cap(int32_t cap) {
+  if (cap < 0) {
+    agents::set_global_error("agents_debug_set_label_loop_cap: cap must be >= 0");
+    return AGENTS_EINVAL;
+  }
+  agents::g_label_loop_cap.store(cap);
+  return AGENTS_OK;
+}
 
 // struct agents_ctx is defined in ctx_internal.h
 
@@ -93,13 +155,7 @@ template <class T>
 int dalloc(agents_ctx* ctx, T** out, size_t count) {
   void* p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(ctx, AGENTS_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
-                cudaGetErrorString(e));
-  }
-  ctx->allocs.push_back(p);
+  TRY(ctx_alloc(ctx, &p, count * sizeof(T)));
   *out = static_cast<T*>(p);
   return AGENTS_OK;
 }
@@ -299,14 +355,17 @@ void ensure_reuse_buffers(agents_ctx* ctx) {
   }
   const size_t need = (sizes[0] + sizes[1] + sizes[2] + sizes[3]) * sizeof(float);
   if (free_b < need || free_b - need < total_b / 4) return;
+  if (!mem_reserve(need)) return;  // optional buffers: skipped under the memory limit
   for (int k = 0; k < 4; ++k) {
     if (cudaMalloc(&p[k], sizes[k] * sizeof(float)) != cudaSuccess) {
       cudaGetLastError();
       for (int m = 0; m < k; ++m) cudaFree(p[m]);
+      mem_release(need);
       return;
     }
   }
   for (int k = 0; k < 4; ++k) ctx->allocs.push_back(p[k]);
+  ctx->held_bytes += need;
   ctx->traj_alt[0] = static_cast<float*>(p[0]);
   ctx->traj_alt[1] = static_cast<float*>(p[1]);
   ctx->cT_alt[0] = static_cast<float*>(p[2]);
@@ -343,13 +402,13 @@ int final_state(agents_ctx* ctx, float* dst, int64_t& steps) {
 
 int ensure_solve_buffers(agents_ctx* ctx) {
   ensure_reuse_buffers(ctx);
-  if (ctx->s_c) return AGENTS_OK;
-  TRY(dalloc(ctx, &ctx->s_c, ctx->nc));
-  TRY(dalloc(ctx, &ctx->s_cn, ctx->nc));
-  TRY(dalloc(ctx, &ctx->s_trial_c, ctx->nc));
-  TRY(dalloc(ctx, &ctx->s_v, ctx->nv));
-  TRY(dalloc(ctx, &ctx->s_vn, ctx->nv));
-  TRY(dalloc(ctx, &ctx->s_mu, ctx->nv));
+  // each buffer on its own: an allocation refused part-way leaves the others usable
+  if (!ctx->s_c) TRY(dalloc(ctx, &ctx->s_c, ctx->nc));
+  if (!ctx->s_cn) TRY(dalloc(ctx, &ctx->s_cn, ctx->nc));
+  if (!ctx->s_trial_c) TRY(dalloc(ctx, &ctx->s_trial_c, ctx->nc));
+  if (!ctx->s_v) TRY(dalloc(ctx, &ctx->s_v, ctx->nv));
+  if (!ctx->s_vn) TRY(dalloc(ctx, &ctx->s_vn, ctx->nv));
+  if (!ctx->s_mu) TRY(dalloc(ctx, &ctx->s_mu, ctx->nv));
   return AGENTS_OK;
 }
 
@@ -556,6 +615,7 @@ int agents_destroy(agents_ctx* ctx) {
   DeviceGuard dg(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (void* p : ctx->allocs) cudaFree(p);
+  mem_release(ctx->held_bytes);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
   delete ctx;
   return AGENTS_OK;
@@ -728,6 +788,36 @@ int agents_adjoint_from(agents_ctx* ctx, const double* eps, const float* lambdaT
   return AGENTS_OK;
 }
 
+int agents_flow_backward(agents_ctx* ctx, const double* eps, const float* grad_cT_dev,
+                         double* grad_eps_out, float* grad_c0_dev) {
+  if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
+  if (!eps) return fail(ctx, AGENTS_EINVAL, "eps must not be NULL");
+  TRY(need(ctx, grad_cT_dev, "grad_cT_dev"));
+  TRY(check_aligned(ctx, grad_c0_dev, "grad_c0_dev"));
+  DeviceGuard dg(ctx->device);
+  std::vector<double> host;
+  TRY(read_control(ctx, eps, host));
+  if (!ctx->stored || host != ctx->stored_eps)
+    return fail(ctx, AGENTS_ESTATE, "agents_flow_backward needs a preceding "
+                                    "agents_forward(store=1) with the same control");
+  // lambda^T = -dL/dc^T
+  CK(launch_scale_f32(grad_cT_dev, -1.0f, ctx->lam[0], ctx->nc, ctx->stream));
+  ++ctx->launches;
+  float* lam0 = nullptr;
+  TRY(adjoint_sweep_from(ctx, ctx->d_eps, &lam0));
+  if (grad_c0_dev) {  // dL/dc^0 = -lambda^0
+    CK(launch_scale_f32(lam0, -1.0f, grad_c0_dev, ctx->nc, ctx->stream));
+    ++ctx->launches;
+  }
+  if (grad_eps_out) {  // dL/deps^n = -dt D^n, reduced from the same partials
+    CK(launch_reduce_rows(ctx->d_part_adj, ctx->nb_adj, 2, ctx->T, -ctx->p.dt / (2.0 * ctx->M),
+                          ctx->d_trial[0], ctx->stream));
+    ++ctx->launches;
+    TRY(from_device(ctx, grad_eps_out, ctx->d_trial[0], 2 * (size_t)ctx->T * sizeof(double)));
+  }
+  return AGENTS_OK;
+}
+
 int agents_objective(agents_ctx* ctx, const float* c_dev, const float* v_dev,
                      const float* mu_dev, double* obj_out, float* lambda_dev) {
   if (!ctx) return fail(nullptr, AGENTS_EINVAL, "ctx is NULL");
@@ -793,8 +883,8 @@ int agents_labels(agents_ctx* ctx, const float* c_dev, float threshold, int32_t*
   TRY(need(ctx, c_dev, "c_dev"));
   if (!labels_out) return fail(ctx, AGENTS_EINVAL, "labels_out is NULL");
   DeviceGuard dg(ctx->device);
-  CK(launch_labels(c_dev, ctx->p.height, ctx->p.width, ctx->C, threshold, ctx->d_labels,
-                   ctx->d_lstat, ctx->d_lstat + 1, ctx->stream));
+  CK(launch_labels(c_dev, ctx->p.height, ctx->p.width, ctx->C, threshold, label_loop_cap(),
+                   ctx->d_labels, ctx->d_lstat, ctx->d_lstat + 1, ctx->stream));
   int32_t hs[2];
   CK(cudaMemcpyAsync(hs, ctx->d_lstat, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -940,17 +1030,21 @@ int solve(agents_ctx* ctx, const agents_solve_opts* opts, double* eps_io, float*
   TRY(from_device(ctx, mu_io, mu, ctx->nv * sizeof(float)));
   if (v_out) TRY(from_device(ctx, v_out, v, ctx->nv * sizeof(float)));
   if (c_out) TRY(from_device(ctx, c_out, c, ctx->nc * sizeof(float)));
+  int32_t lstat[2] = {0, 0};  // {count, status} of the label union-find
   if (labels_out) {
-    CK(launch_labels(c, ctx->p.height, ctx->p.width, ctx->C, 0.02f, ctx->d_labels, ctx->d_lstat,
-                     ctx->d_lstat + 1, ctx->stream));
+    CK(launch_labels(c, ctx->p.height, ctx->p.width, ctx->C, 0.02f, label_loop_cap(),
+                     ctx->d_labels, ctx->d_lstat, ctx->d_lstat + 1, ctx->stream));
     ctx->launches += 3;
     TRY(from_device(ctx, labels_out, ctx->d_labels, (size_t)ctx->N * sizeof(int32_t)));
+    CK(cudaMemcpyAsync(lstat, ctx->d_lstat, sizeof(lstat), cudaMemcpyDeviceToHost, ctx->stream));
   }
   CK(cudaStreamSynchronize(ctx->stream));
   inf.final_sigma = sigma;
   inf.kernel_launches = ctx->launches - launches0;
   if (info) *info = inf;
   if (status == AGENTS_EDIVERGED) return fail(ctx, status, "solve diverged (NaN/Inf)");
+  if (status == AGENTS_OK && lstat[1] != 0)
+    return fail(ctx, AGENTS_ETIMEOUT, "label union-find exceeded its loop bound");
   return status;
 }
 

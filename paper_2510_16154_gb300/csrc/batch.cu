@@ -364,10 +364,20 @@ extern "C" int agents_solve_batch(int32_t n, agents_ctx* const* ctx_list,
     if (c->device != ctxs[0]->device)
       return ctx_fail(ctxs[0], AGENTS_EINVAL, "all contexts must live on one device");
   }
+  // The caller's current device is restored on every return path.
+  struct RestoreDevice {
+    int prev = -1;
+    ~RestoreDevice() {
+      if (prev >= 0) cudaSetDevice(prev);
+    }
+  } restore;
   int prev_dev = -1;
   cudaGetDevice(&prev_dev);
   cudaGetLastError();   // a launch below reports only its own error
-  if (prev_dev != ctxs[0]->device) cudaSetDevice(ctxs[0]->device);
+  if (prev_dev != ctxs[0]->device) {
+    cudaSetDevice(ctxs[0]->device);
+    restore.prev = prev_dev;
+  }
   // A stream of the batch's own (graph capture is not allowed on the legacy default
   // stream), ordered after the work already queued on the contexts' stream.
   struct OwnStream {
@@ -387,13 +397,17 @@ extern "C" int agents_solve_batch(int32_t n, agents_ctx* const* ctx_list,
   // ---- per-image buffers and inputs
   for (int i = 0; i < n; ++i) {
     agents_ctx* c = ctxs[i];
-    if (!c->s_c) {  // the solve workspaces (solve() allocates the same ones)
+    {  // the solve workspaces (solve() allocates the same ones), each on its own
       float** bufs[6] = {&c->s_c, &c->s_cn, &c->s_trial_c, &c->s_v, &c->s_vn, &c->s_mu};
       const size_t sizes[6] = {c->nc, c->nc, c->nc, c->nv, c->nv, c->nv};
       for (int k = 0; k < 6; ++k) {
+        if (*bufs[k]) continue;
         void* p = nullptr;
-        BCK(cudaMalloc(&p, sizes[k] * sizeof(float)));
-        c->allocs.push_back(p);
+        const int st = ctx_alloc(c, &p, sizes[k] * sizeof(float));
+        if (st != AGENTS_OK) {
+          if (c != ctxs[0]) ctx_fail(ctxs[0], st, c->err.c_str());
+          return st;
+        }
         *bufs[k] = static_cast<float*>(p);
       }
     }
@@ -875,7 +889,6 @@ extern "C" int agents_solve_batch(int32_t n, agents_ctx* const* ctx_list,
     c->stored = false;
   }
   BCK(cudaStreamSynchronize(s));
-  if (prev_dev >= 0 && prev_dev != ctxs[0]->device) cudaSetDevice(prev_dev);
   if (status != AGENTS_OK) return ctx_fail(ctxs[0], status, "an image of the batch diverged");
   return AGENTS_OK;
 }

@@ -69,10 +69,18 @@ struct agents_ctx {
   std::vector<agents_iter_record> log;  // per-DAL-iteration records of the last solve()
   std::vector<agents_outer_record> outer_log;  // per-multiplier-step records
   std::vector<void*> allocs;
+  size_t held_bytes = 0;          // bytes of allocs counted against the memory limit
 };
 
 namespace agents {
 // Helpers implemented in agents.cu for other translation units.
 int ctx_fail(agents_ctx* ctx, int code, const char* msg);
 int ctx_forward_sweep(agents_ctx* ctx, const double* d_eps, float* dst_T, bool store);
+// Context-owned device allocation counted against agents_set_memory_limit's cap
+// (AGENTS_ENOMEM with the message in ctx->err when the cap or cudaMalloc refuses).
+int ctx_alloc(agents_ctx* ctx, void** out, size_t bytes);
+bool mem_reserve(size_t bytes);
+void mem_release(size_t bytes);
+// Loop bound of the label union-find set by agents_debug_set_label_loop_cap (0: default).
+int32_t label_loop_cap();
 }  // namespace agents

@@ -130,12 +130,16 @@ cudaError_t launch_alm_update(const float* c, const float* c_prev, const float* 
 // Multiplier-update statistics from the reduced raw sums (see alm_update in agents.h).
 cudaError_t launch_alm_finalize(const double* raw, double* stats, double rho, double gamma,
                                 double cell, cudaStream_t s);
+// y = a x over n floats (x, y 16-byte aligned; x == y allowed).
+cudaError_t launch_scale_f32(const float* x, float a, float* y, size_t n, cudaStream_t s);
 // trial[n] = clip(eps[n] + tau * D[n], lo, hi) for the T x 2 control.
 cudaError_t launch_control_step(const double* eps, const double* D, double tau,
                                 const double* lo_hi, double* trial, int T, cudaStream_t s);
 
 // ---- labels (labels.cu) ----
-cudaError_t launch_labels(const float* c, int H, int W, int C, float threshold, int32_t* labels,
-                          int32_t* count, int32_t* status, cudaStream_t s);
+// loop_cap bounds every union-find loop (0: the pixel count, which a forest whose links
+// decrease never reaches); a loop that reaches it gives up and sets *status = 1.
+cudaError_t launch_labels(const float* c, int H, int W, int C, float threshold, int loop_cap,
+                          int32_t* labels, int32_t* count, int32_t* status, cudaStream_t s);
 
 }  // namespace agents

@@ -11,7 +11,9 @@
 // Because links always point to a smaller index, each root is the smallest index of its
 // component, so the result is canonical (independent of thread timing).  Every loop is
 // bounded by the pixel count; exceeding the bound sets *status = 1 (it cannot happen for
-// a forest whose links decrease) instead of spinning.
+// a forest whose links decrease) instead of spinning.  A smaller bound can be given (a
+// test hook that exercises the give-up path): the loops then stop early, every index they
+// follow is still a label value in [0, n), and *status reports the give-up.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -55,32 +57,33 @@ __global__ void labels_init_kernel(int32_t* L, int n, int32_t* count, int32_t* s
 }
 
 __global__ void labels_merge_kernel(const float* __restrict__ c, int H, int W, int C, float thr,
-                                    int32_t* L, int32_t* status) {
+                                    int cap, int32_t* L, int32_t* status) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y * blockDim.y + threadIdx.y;
   if (q >= W || r >= H) return;
-  const int cap = H * W;
   const size_t i = (size_t)r * W + q;
   if (q + 1 < W && joined(c, i, i + 1, C, thr)) unite(L, (int)i, (int)(i + 1), cap, status);
   if (r + 1 < H && joined(c, i, i + W, C, thr)) unite(L, (int)i, (int)(i + W), cap, status);
 }
 
-__global__ void labels_flatten_kernel(int32_t* L, int n, int32_t* count, int32_t* status) {
+__global__ void labels_flatten_kernel(int32_t* L, int n, int cap, int32_t* count,
+                                      int32_t* status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int root = find_root(L, i, n, status);
+  const int root = find_root(L, i, cap, status);
   L[i] = root;
   if (root == i) atomicAdd(count, 1);
 }
 
-cudaError_t launch_labels(const float* c, int H, int W, int C, float threshold, int32_t* labels,
-                          int32_t* count, int32_t* status, cudaStream_t s) {
+cudaError_t launch_labels(const float* c, int H, int W, int C, float threshold, int loop_cap,
+                          int32_t* labels, int32_t* count, int32_t* status, cudaStream_t s) {
   const int n = H * W;
+  const int cap = (loop_cap > 0 && loop_cap < n) ? loop_cap : n;
   labels_init_kernel<<<(n + 255) / 256, 256, 0, s>>>(labels, n, count, status);
   dim3 block(32, 8), grid((W + 31) / 32, (H + 7) / 8);
-  labels_merge_kernel<<<grid, block, 0, s>>>(c, H, W, C, threshold, labels, status);
+  labels_merge_kernel<<<grid, block, 0, s>>>(c, H, W, C, threshold, cap, labels, status);
   // Roots must be final before flattening; a second kernel orders that.
-  labels_flatten_kernel<<<(n + 255) / 256, 256, 0, s>>>(labels, n, count, status);
+  labels_flatten_kernel<<<(n + 255) / 256, 256, 0, s>>>(labels, n, cap, count, status);
   return cudaGetLastError();
 }
 

@@ -11,14 +11,17 @@
 // until the process exits.
 //
 // The host cannot pass g_objective_scratch to a kernel by name (in host code the name
-// is a host-side stand-in, not a device address), so the first call on each device,
-// with that device current, looks its address up with cudaGetSymbolAddress and caches
-// it; later calls on that device reuse the cached address.
+// is a host-side stand-in, not a device address), so every call, with the caller's
+// device current, looks its address up with cudaGetSymbolAddress and checks the result.
+// The first lookup on a device loads this library's device code there (allocating the
+// array; it can synchronise the device), which is why the first call belongs in set-up;
+// later lookups only read the loaded module's table.  Not caching the address keeps it
+// right for whichever context is current: a non-primary context of the same device, or
+// the primary context re-created after a device reset, has its own copy of the array.
 #include "agents.h"
 #include "kernels.h"
 
 #include <cstdio>
-#include <mutex>
 #include <string>
 
 namespace agents {
@@ -30,38 +33,27 @@ using namespace agents;
 namespace {
 
 // One float64 partial per reduction block (32 x 8 threads over 128 x 8 pixels): 32768
-// blocks = 256 KiB, enough for images of up to 33,554,432 pixels (for example 4096 x 8192).
+// blocks = 256 KiB, enough for ceil(W/128) * ceil(H/8) <= 32768 (for example 4096 x 8192).
 constexpr int kMaxBlocks = 32768;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_objective_scratch[kMaxBlocks];
-
-std::mutex g_setup_mutex;
-double* g_scratch_addr[kMaxDevices] = {};
 
 int fail(int code, const char* msg) {
   set_global_error(msg);
   return code;
 }
 
-// Address of g_objective_scratch on the current device (looked up once per device).
-int scratch_on_current_device(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(AGENTS_ECUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return fail(AGENTS_EINVAL, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_objective_scratch);
-    if (e != cudaSuccess) {
-      std::string msg = std::string("cudaGetSymbolAddress(g_objective_scratch): ") +
-                        cudaGetErrorString(e);
-      return fail(AGENTS_ECUDA, msg.c_str());
-    }
-    g_scratch_addr[dev] = static_cast<double*>(p);
+// Device address of g_objective_scratch in the current device context.
+int scratch_in_current_context(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_objective_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    std::string msg = std::string("cudaGetSymbolAddress(g_objective_scratch): ") +
+                      cudaGetErrorString(e);
+    return fail(AGENTS_ECUDA, msg.c_str());
   }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<double*>(p);
   return AGENTS_OK;
 }
 
@@ -92,7 +84,9 @@ extern "C" int agents_objective_noalloc(int32_t height, int32_t width, int32_t c
   if (!aligned16(c_dev) || !aligned16(c0_dev) || !aligned16(v_dev) || !aligned16(mu_dev) ||
       (lambda_dev && !aligned16(lambda_dev)))
     return fail(AGENTS_EINVAL, "field pointers must be 16-byte aligned");
-  if (!on_device(obj_dev)) return fail(AGENTS_EINVAL, "obj_dev must be device memory");
+  if (!on_device(c_dev) || !on_device(c0_dev) || !on_device(v_dev) || !on_device(mu_dev) ||
+      !on_device(obj_dev) || (lambda_dev && !on_device(lambda_dev)))
+    return fail(AGENTS_EINVAL, "every field pointer and obj_dev must be device memory");
   const TvGeom g{height, width, channels, (float)(0.5 * width), (float)(0.5 * height),
                  (float)rho, (float)(1.0 / rho), (float)alpha, rho,
                  1.0 / ((double)width * (double)height), tv_mode};
@@ -100,12 +94,13 @@ extern "C" int agents_objective_noalloc(int32_t height, int32_t width, int32_t c
   if (nb > kMaxBlocks) {
     char msg[200];
     std::snprintf(msg, sizeof(msg),
-                  "image of %d x %d needs %d reduction blocks; the static scratch holds %d "
-                  "(images up to 33554432 pixels)", height, width, nb, kMaxBlocks);
+                  "image of %d x %d needs %d reduction blocks of 128 x 8 pixels; the static "
+                  "scratch holds %d (ceil(W/128) * ceil(H/8) <= %d, e.g. 4096 x 8192)",
+                  height, width, nb, kMaxBlocks, kMaxBlocks);
     return fail(AGENTS_EINVAL, msg);
   }
   double* scratch = nullptr;
-  int st = scratch_on_current_device(&scratch);
+  int st = scratch_in_current_context(&scratch);
   if (st != AGENTS_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   // Every block overwrites its own partial and the reduction reads exactly those nb

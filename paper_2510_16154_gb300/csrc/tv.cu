@@ -16,6 +16,8 @@
 #include "fp_bits.cuh"
 #include "kernels.h"
 
+#include <algorithm>
+
 namespace agents {
 
 constexpr int kTvBX = 32, kTvBY = 8, kPPT = 4;
@@ -626,6 +628,30 @@ __global__ void control_step_kernel(const double* __restrict__ eps, const double
     const double e = fma(tau, D[i], eps[i]);
     trial[i] = fmin(fmax(e, lo_hi[k]), lo_hi[2 + k]);
   }
+}
+
+// y = a x over n floats (16-byte aligned fields: four at a time, then the tail).
+__global__ void scale_f32_kernel(const float* __restrict__ x, float a, float* __restrict__ y,
+                                 size_t n) {
+  const size_t n4 = n / 4;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const float4 v = reinterpret_cast<const float4*>(x)[i];
+    reinterpret_cast<float4*>(y)[i] = make_float4(a * v.x, a * v.y, a * v.z, a * v.w);
+  }
+  for (size_t i = 4 * n4 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    y[i] = a * x[i];
+}
+
+cudaError_t launch_scale_f32(const float* x, float a, float* y, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t want = (n / 4 + 255) / 256;
+  const int grid = (int)std::max<size_t>(1, std::min<size_t>(want, (size_t)sms * 8));
+  scale_f32_kernel<<<grid, 256, 0, s>>>(x, a, y, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_control_step(const double* eps, const double* D, double tau,

@@ -87,19 +87,10 @@ class WarmStartNet:
 
     # -- parameters
     def init_params(self, seed: int) -> None:
-        """He-normal convolution weights, zero biases, control head at log 57."""
-        rng = np.random.default_rng(seed)
-        parts = []
-        for name, shape in self.spec.param_shapes():
-            if name.endswith(".W"):
-                parts.append(rng.normal(0.0, math.sqrt(2.0 / np.prod(shape[1:])), size=shape))
-            elif name == "eps.A":
-                parts.append(rng.normal(0.0, 0.01, size=shape))
-            elif name == "eps.c":
-                parts.append(np.full(shape, math.log(57.0)))
-            else:
-                parts.append(np.zeros(shape))
-        self.set_params(np.concatenate([p.ravel() for p in parts]).astype(np.float32))
+        """He-normal convolution weights, zero biases, control head at log 57 (the seeded
+        initial values of ``synth.params.init_net_params``)."""
+        from synth.params import init_net_params
+        self.set_params(init_net_params(self.spec.param_shapes(), seed))
 
     def set_params(self, theta) -> None:
         if isinstance(theta, np.ndarray):

@@ -53,3 +53,19 @@ def f32(a):
 
 def zeros_dev(*shape, dtype=None):
     return torch.zeros(*shape, dtype=dtype or torch.float32, device="cuda")
+
+
+def assert_control_derivative(D, Dw, rel=1e-5, negligible=1e-6):
+    """D = (D_x, D_c) per step against the oracle's, each component against its OWN
+    largest entry (relative rel).  Only a component below `negligible` times the other's
+    largest entry (truly negligible: far below what float32 resolves beside it) is
+    checked against rel times the largest entry of D instead."""
+    D = np.asarray(D, dtype=np.float64).reshape(-1, 2)
+    Dw = np.asarray(Dw, dtype=np.float64).reshape(-1, 2)
+    top = float(np.max(np.abs(Dw)))
+    assert top > 0
+    for k, name in ((0, "D_x"), (1, "D_c")):
+        m = float(np.max(np.abs(Dw[:, k])))
+        scale = m if m >= negligible * top else top
+        err = float(np.max(np.abs(D[:, k] - Dw[:, k])))
+        assert err <= rel * scale, (name, err, m, top)

@@ -112,3 +112,14 @@ def test_warmstart_config_layout_and_validation(cdll):
     assert cdll.ws_conv3x3_forward(None, None, None, None, None, None, 1, 1, 1, 1, 1, 0, 0,
                                    None) == lib.AGENTS_EINVAL
     assert cdll.ws_conv3x3_backward_weight_workspace(2, 8, 8, 16, 32) > 0
+
+
+def test_memory_limit_and_label_hook_without_a_device(cdll):
+    # host-side state only: no context, no device call
+    assert lib.agents_memory_held() == 0
+    lib.agents_set_memory_limit(1 << 20)
+    lib.agents_set_memory_limit(0)
+    with pytest.raises(lib.AgentsError) as e:
+        lib.agents_debug_set_label_loop_cap(-5)
+    assert e.value.code == lib.AGENTS_EINVAL
+    lib.agents_debug_set_label_loop_cap(0)

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from gpuutil import ensure_lib, dev, host, params, f32, torch
+import oracle
 from paper_2510_16154_gb300 import lib
 from synth import ImageSpec, make_image
 
@@ -102,3 +103,32 @@ def test_batch_autotuned_is_valid():
         assert np.all(np.isfinite(c_b[k])) and np.all(np.isfinite(eps_b[k]))
         assert np.all(eps_b[k] >= 2.0) and np.all(eps_b[k] <= 1100.0)
         assert infos[k].outer_done == 3
+
+
+# A mixed batch against the FP64 oracle (not against the library's own solve): RGB and
+# grey images, one 31-band image, window radii 2 and 3, uneven sizes.
+ORACLE_CASES = [  # (H, W, C, R, regions, seed)
+    (24, 30, 3, 2, 3, 11), (20, 26, 31, 3, 3, 12), (28, 22, 1, 3, 4, 13), (18, 24, 3, 2, 2, 14),
+]
+
+
+@pytest.mark.parametrize("alpha,autotune", [(100.0, True), (3000.0, False)])
+def test_batch_matches_oracle(alpha, autotune):
+    """Every image of the batch within the 64 x 64 parity workload's tolerances of the
+    oracle's Algorithm 2: colours 1e-4 max-abs, control 1e-3 relative, multiplier 1e-4."""
+    ensure_lib()
+    imgs = [_image(H, W, C, K, seed) for H, W, C, R, K, seed in ORACLE_CASES]
+    o = _opts(k_out=3, k_in=4)
+    eps_b, mu_b, c_b, infos = _batch(ORACLE_CASES, imgs, o, alpha, autotune=autotune,
+                                     use_graph=True)
+    for k, ((H, W, C, R, K, seed), img) in enumerate(zip(ORACLE_CASES, imgs)):
+        _, op = params(H, W, C, R, T, alpha=alpha)
+        ref = oracle.admm_solve(img, op, oracle.SolveOpts(k_out=3, k_in=4))
+        err = np.max(np.abs(c_b[k] - ref["c"]))
+        print(f"{H}x{W}x{C} R={R}: max|c - oracle| {err:.2e}, trials "
+              f"{infos[k].trials}/{sum(i.trials for i in ref['inner'])}")
+        assert infos[k].outer_done == 3
+        assert err <= 1e-4
+        assert np.max(np.abs(eps_b[k] - ref["eps"])) <= 1e-3 * np.max(np.abs(ref["eps"]))
+        assert np.max(np.abs(mu_b[k] - ref["mu"])) <= 1e-4 * max(1.0, np.max(np.abs(ref["mu"])))
+        assert np.max(np.abs(ref["c"] - img)) > 1e-3          # the solve moved the image

@@ -122,20 +122,28 @@ def test_constant_image_solve_stalls():
     assert np.all(out["labels"] == 0)
 
 
-def _ambiguous_edges_only(c_gpu, c_ref, tie, thr=0.02):
-    """True if every 4-neighbour pair joined on one side and not on the other has a
-    max-channel colour difference within `tie` of the threshold on the reference side."""
+def _differing_join_decisions(c_gpu, c_ref, thr=0.02):
+    """Max-channel colour differences (reference side) of every 4-neighbour pair that is
+    joined on one side and not on the other."""
     g = np.asarray(c_gpu, dtype=np.float32)
     r = np.asarray(c_ref).astype(np.float32)
     t = np.float32(thr)
+    out = []
     for sl_a, sl_b in (((slice(None), slice(1, None)), (slice(None), slice(None, -1))),
                        ((slice(1, None), slice(None)), (slice(None, -1), slice(None)))):
         dg = np.max(np.abs(g[sl_a] - g[sl_b]), axis=-1)
         dr = np.max(np.abs(r[sl_a] - r[sl_b]), axis=-1)
         differ = (dg <= t) != (dr <= t)
-        if np.any(np.abs(dr[differ].astype(np.float64) - thr) > tie):
-            return False
-    return True
+        out.extend(dr[differ].astype(np.float64).tolist())
+    return np.array(out)
+
+
+# The one declared deviation from "equal cluster count": at alpha = 3000 the 64 x 64 seed-0
+# workload ends with ~3900 near-singleton clusters, and a neighbour pair whose largest
+# channel difference lies within the colour tolerance of the 0.02 threshold may be joined
+# on one side only.  Accepted there alone, for at most this many such pairs, each within
+# twice the measured max|c - c_oracle| of the threshold.
+TIE_SEED, TIE_ALPHA, MAX_TIE_PAIRS = 0, 3000.0, 4
 
 
 @pytest.mark.parametrize("alpha", [3000.0, 100.0])
@@ -144,9 +152,10 @@ def test_parity_64_rgb_full_solve(seed, alpha):
     """64x64x3, 4 Voronoi regions, sigma 0.05; R = 2, T = 20, 30 DAL iterations per
     multiplier step, 10 multiplier steps, against the stored FP64 oracle run (written by
     tests/golden/make_oracle_parity.py).  Colours within 1e-4 max-abs; cluster labels
-    agree on >= 99.9% of pixels with equal count (at alpha = 3000, where the solve leaves
-    ~3900 near-singleton clusters, a count difference is accepted only if every neighbour
-    pair decided differently is a threshold tie within the colour tolerance).
+    agree on >= 99.9% of pixels with equal count, except in the one declared case
+    (seed 0 at alpha = 3000, ~3900 near-singleton clusters): there a count difference is
+    accepted only for at most MAX_TIE_PAIRS neighbour pairs decided differently, each a
+    threshold tie within twice the colour error.
 
     Late Armijo tests can sit within float32 rounding of the state (relative differences
     of L~ near 1e-8, mostly at alpha = 3000), so the two decision traces may part; such
@@ -180,13 +189,15 @@ def test_parity_64_rgb_full_solve(seed, alpha):
           f"same-trace {same:.3f}")
     assert err <= 1e-4
     assert agree >= 0.999
-    if alpha == 100.0:
-        assert n_gpu == int(ref["count"])
-    else:
-        # ~3900 near-singleton clusters: every neighbour pair whose join decision differs
-        # must be a tie within the colour tolerance (|max-channel diff - 0.02| <= 2 err)
-        amb = _ambiguous_edges_only(c, ref["c"], tie=2.0 * err)
-        assert n_gpu == int(ref["count"]) or amb
+    ties = _differing_join_decisions(c, ref["c"])
+    print(f"  pairs decided differently: {len(ties)} "
+          f"(max |diff - 0.02| {np.max(np.abs(ties - 0.02)) if len(ties) else 0.0:.2e})")
+    if n_gpu != int(ref["count"]):
+        # only the declared deviation: seed 0 at alpha = 3000, a bounded number of
+        # threshold ties
+        assert (seed, alpha) == (TIE_SEED, TIE_ALPHA)
+        assert 0 < len(ties) <= MAX_TIE_PAIRS
+        assert np.all(np.abs(ties - 0.02) <= 2.0 * err)
     assert info.outer_done == 10
     # the primal-dual gap of the last multiplier step is below that of the first
     assert info.final_gap < ref["gap"][0]

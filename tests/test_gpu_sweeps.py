@@ -2,8 +2,10 @@
 against the FP64 oracle, through the C ABI.
 
 Tolerances: one forward step <= 1e-6 max-abs on colours in [0, 1]; a 20-step sweep
-<= 1e-5; adjoint state and control derivative <= 1e-5 relative to their largest entry
-(normwise: single entries can be orders of magnitude below the rest).  Shapes span
+<= 1e-5; adjoint state <= 1e-5 relative to its largest entry; the control derivative
+<= 1e-5 relative per component: D_x against its own largest entry and D_c against its
+own (a component is checked against the largest entry of D only where it is below 1e-6
+of the other, which none of these cases reaches).  Shapes span
 several 64 x 8 / 64 x 4 tiles with ragged tails, the border-only case of images smaller
 than one window, the generic kernel (C = 5, R = 9), the wide-channel kernel (C = 31,
 R = 2..7, 32 x 4 tiles), and the full 1024 x 1024 x 3, R = 5
@@ -12,7 +14,8 @@ launch the benchmark times (checked on sampled pixels and on one full adjoint st
 import numpy as np
 import pytest
 
-from gpuutil import ensure_lib, dev, host, params, f32, zeros_dev, torch
+from gpuutil import (ensure_lib, dev, host, params, f32, zeros_dev, torch,
+                     assert_control_derivative)
 import oracle
 from paper_2510_16154_gb300 import lib
 from synth import ImageSpec, make_image
@@ -163,7 +166,10 @@ def test_adjoint_sweep(H, W, C, R, T):
     p, op = params(H, W, C, R, T, alpha=40.0, rho=0.5, gamma=0.5)
     D, obj, lam0 = _run_adjoint(p, c0, v, mu, eps)
     Dw, objw, lamw = _oracle_adjoint(op, c0, v, mu, eps)
-    assert np.max(np.abs(D - Dw)) <= 1e-5 * np.max(np.abs(Dw))
+    print(f"max|D_x| {np.max(np.abs(Dw[:, 0])):.3e} max|D_c| {np.max(np.abs(Dw[:, 1])):.3e} "
+          f"rel err D_x {np.max(np.abs(D[:, 0] - Dw[:, 0])) / np.max(np.abs(Dw[:, 0])):.2e} "
+          f"D_c {np.max(np.abs(D[:, 1] - Dw[:, 1])) / np.max(np.abs(Dw[:, 1])):.2e}")
+    assert_control_derivative(D, Dw)
     assert obj == pytest.approx(objw, rel=1e-6)
     assert np.max(np.abs(lam0 - lamw)) <= 1e-5 * np.max(np.abs(lamw))
     assert np.max(np.abs(Dw)) > 0
@@ -217,7 +223,8 @@ def test_full_size_adjoint_step():
     c1 = oracle.forward_final(c0, eps, op)
     lamT = oracle.terminal_adjoint(c1, v, mu, c0, op)
     Dw = oracle.control_derivative(c0, lamT, 57.0, 57.0, op)
-    assert np.max(np.abs(D[0] - Dw)) <= 1e-5 * np.max(np.abs(Dw))
+    print(f"D {D[0]} oracle {Dw}")
+    assert_control_derivative(D[0], Dw)
     rows = list(rng.integers(0, 1024, 200)) + [0, 1023, 0, 1023]
     cols = list(rng.integers(0, 1024, 200)) + [0, 1023, 1023, 0]
     want = lamT[rows, cols] + op.dt * oracle.jacobian_transpose_apply_at(c0, lamT, rows, cols,
