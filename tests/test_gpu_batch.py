@@ -45,13 +45,13 @@ def _single(H, W, C, R, img, o, alpha):
     return eps, mu, c, info
 
 
-def _batch(cases, imgs, o, alpha, **kw):
+def _batch(cases, imgs, o, alpha, eps0=57.0, **kw):
     ctxs, eps, mus, cs = [], [], [], []
     try:
         for (H, W, C, R, K, seed), img in zip(cases, imgs):
             p, _ = params(H, W, C, R, T, alpha=alpha)
             ctxs.append(lib.Context(p, dev(img, np.float32)))
-            eps.append(np.full((T, 2), 57.0))
+            eps.append(np.full((T, 2), eps0))
             mus.append(np.zeros((H, W, 2, C), dtype=np.float32))
             cs.append(np.zeros((H, W, C), dtype=np.float32))
         infos = lib.agents_solve_batch([c.handle for c in ctxs], o, eps, mus, cs, **kw)
@@ -112,23 +112,30 @@ ORACLE_CASES = [  # (H, W, C, R, regions, seed)
 ]
 
 
-@pytest.mark.parametrize("alpha,autotune", [(100.0, True), (3000.0, False)])
+@pytest.mark.parametrize("alpha,autotune", [(10.0, True), (300.0, False)])
 def test_batch_matches_oracle(alpha, autotune):
     """Every image of the batch within the 64 x 64 parity workload's tolerances of the
-    oracle's Algorithm 2: colours 1e-4 max-abs, control 1e-3 relative, multiplier 1e-4."""
+    oracle's Algorithm 2 started from the same control (eps = 8, where the 31-band colours
+    interact): colours 1e-4 max-abs, control 1e-3 relative, multiplier 1e-4.  At
+    alpha = 10 the solves smooth the images (the control goes to the lower bound of E);
+    at alpha = 300 they mostly keep them."""
     ensure_lib()
     imgs = [_image(H, W, C, K, seed) for H, W, C, R, K, seed in ORACLE_CASES]
     o = _opts(k_out=3, k_in=4)
-    eps_b, mu_b, c_b, infos = _batch(ORACLE_CASES, imgs, o, alpha, autotune=autotune,
-                                     use_graph=True)
+    eps_b, mu_b, c_b, infos = _batch(ORACLE_CASES, imgs, o, alpha, eps0=8.0,
+                                     autotune=autotune, use_graph=True)
+    moved = []
     for k, ((H, W, C, R, K, seed), img) in enumerate(zip(ORACLE_CASES, imgs)):
         _, op = params(H, W, C, R, T, alpha=alpha)
-        ref = oracle.admm_solve(img, op, oracle.SolveOpts(k_out=3, k_in=4))
+        ref = oracle.admm_solve(img, op, oracle.SolveOpts(k_out=3, k_in=4),
+                                eps0=np.full((T, 2), 8.0))
         err = np.max(np.abs(c_b[k] - ref["c"]))
-        print(f"{H}x{W}x{C} R={R}: max|c - oracle| {err:.2e}, trials "
+        moved.append(np.max(np.abs(ref["c"] - img)))
+        print(f"{H}x{W}x{C} R={R}: max|c - oracle| {err:.2e}, moved {moved[-1]:.2e}, trials "
               f"{infos[k].trials}/{sum(i.trials for i in ref['inner'])}")
         assert infos[k].outer_done == 3
         assert err <= 1e-4
         assert np.max(np.abs(eps_b[k] - ref["eps"])) <= 1e-3 * np.max(np.abs(ref["eps"]))
         assert np.max(np.abs(mu_b[k] - ref["mu"])) <= 1e-4 * max(1.0, np.max(np.abs(ref["mu"])))
-        assert np.max(np.abs(ref["c"] - img)) > 1e-3          # the solve moved the image
+    if alpha == 10.0:
+        assert sorted(moved)[-3] > 0.1      # three of the four images (the 31-band one too)
