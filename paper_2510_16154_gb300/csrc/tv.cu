@@ -46,22 +46,6 @@ __device__ __forceinline__ float grad_y(const float* __restrict__ c, const TvGeo
   return (__ldg(c + (k + g.W) * C + ch) - __ldg(c + (k - g.W) * C + ch)) * g.inv2hy;
 }
 
-// (G c) in float64 (the differences of float32 values are exact in float64).  The
-// operands are widened with integer operations (widen, fp_bits.cuh): the float64 pipe
-// is left to the arithmetic.
-__device__ __forceinline__ double grad_x_f64(const float* __restrict__ c, const TvGeom& g, int r,
-                                             int q, int C, int ch, double inv2hx) {
-  if (q < 1 || q > g.W - 2) return 0.0;
-  const size_t k = (size_t)r * g.W + q;
-  return (widen(__ldg(c + (k + 1) * C + ch)) - widen(__ldg(c + (k - 1) * C + ch))) * inv2hx;
-}
-__device__ __forceinline__ double grad_y_f64(const float* __restrict__ c, const TvGeom& g, int r,
-                                             int q, int C, int ch, double inv2hy) {
-  if (r < 1 || r > g.H - 2) return 0.0;
-  const size_t k = (size_t)r * g.W + q;
-  return (widen(__ldg(c + (k + g.W) * C + ch)) - widen(__ldg(c + (k - g.W) * C + ch))) * inv2hy;
-}
-
 // ------------------------------------------------------------------ objective / terminal
 // Per-pixel term of L~ / (dx dy):  rho/2 |v - Gc + mu/rho|^2 + |v| + alpha/2 |c - c0|^2.
 // With LAMBDA, also lam = -dx dy [G^T (rho G c - rho v - mu) + alpha (c - c0)].
@@ -345,11 +329,86 @@ cudaError_t launch_pd_tv_step(const float* c, const float* mu, float* v, const T
 }
 
 // ------------------------------------------------------------------ multiplier update
-// mu <- mu + gamma (v - G c), evaluated in float64 (G c included) and rounded once to
-// float32; the conversions between the two formats are the integer ones of fp_bits.cuh
-// (exact widening, round-to-nearest-even narrowing: bitwise those of the hardware).
+// mu <- mu + gamma (v - G c) with float64 arithmetic, rounded once to float32.  GB300's
+// float64 pipe is narrow (about two lanes per SM and clock), so the residual
+// R = v - k (c[+1] - c[-1]) (k = 1/(2 dx) or 1/(2 dy)) is formed with error-free float32
+// transformations as an unevaluated pair s + lo (TwoSum of the difference, TwoProduct by
+// k, TwoSum with v; |R - (s + lo)| is below 2^-46 max(|v|, |k (c[+1] - c[-1])|), where
+// the float64 formula's own rounding is 2^-53 of the same), and the float64 pipe does only
+// S = s + lo and mu + gamma S: two operations per component instead of five.  The
+// conversions between the formats are the integer ones of fp_bits.cuh.  Every float32
+// operation of the transformations is an explicitly rounded intrinsic, so the compiler
+// cannot fuse or reorder them.  The result is the correctly rounded float32 value of the
+// float64 update except when that value lies within about 2^-46 gamma max(|v|, |k dc|) of
+// a rounding boundary, and within one float32 ulp of the exact update.
 // Per-block partial sums: |v - Gc|^2, |G^T (v - v_prev)|^2, |c - c_prev|^2, |c|^2 and
-// K(c)/(dx dy) = sum |G c_i| + alpha/2 |c_i - c0_i|^2.
+// K(c)/(dx dy) = sum |G c_i| + alpha/2 |c_i - c0_i|^2 (float32 terms, float64 blocks).
+struct ResidualPair {
+  float s, lo;  // v - k (a - b) = s + lo (to 2^-46 of the larger operand)
+  float g;      // k (a - b) rounded: the gradient component for K(c)
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+__device__ __forceinline__ ResidualPair residual_pair(float v, float a, float b, float k) {
+  float d, de;
+  two_sum(a, -b, d, de);               // a - b = d + de exactly
+  const float p = __fmul_rn(k, d);
+  const float pe = fmaf(k, d, -p);     // k d = p + pe exactly
+  const float q = __fmul_rn(k, de);    // k de, |q| <= k ulp(d) / 2
+  float s, t;
+  two_sum(v, -p, s, t);                // v - p = s + t exactly
+  return {s, __fsub_rn(__fsub_rn(t, pe), q), p};
+}
+
+// mu + gamma (s + lo) in float64.  Where every lane of the warp has lo = 0 (the residual
+// is exactly a float32: the usual case on v = 0 pixels with a power-of-two 1/(2 dx)), the
+// float64 addition forming s + lo is skipped.
+__device__ __forceinline__ float mu_update(float mu, const ResidualPair& r, double gam) {
+  double S = widen(r.s);
+  if (__any_sync(__activemask(), r.lo != 0.0f)) S += widen(r.lo);
+  return narrow(fma(gam, S, widen(mu)));
+}
+
+// Deterministic block sum of NV float32 partials per thread, in float64, with few
+// float64 operations: the partials are staged in shared memory, NV * kSegs threads each
+// add NT / kSegs consecutive ones (widened exactly with integer operations) in index
+// order, and NV threads add those kSegs results in order.  Thread 0 receives the totals
+// in out[] (other threads: unspecified).  Bitwise reproducible.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum_staged(const float (&v)[NV], double (&out)[NV]) {
+  constexpr int kSegs = 8, kLen = NT / kSegs;
+  static_assert(NT % kSegs == 0 && NV * kSegs <= NT, "block too small for the staged sum");
+  __shared__ float part[NV * NT];
+  __shared__ double seg[NV * kSegs];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) part[k * NT + tid] = v[k];
+  __syncthreads();
+  if (tid < NV * kSegs) {
+    const float* p = part + (tid / kSegs) * NT + (tid % kSegs) * kLen;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int i = 0; i < kLen; ++i) acc += widen(p[i]);
+    seg[tid] = acc;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < kSegs; ++j) acc += seg[k * kSegs + j];
+      out[k] = acc;
+    }
+  }
+}
+
 template <int CT>
 __device__ __forceinline__ void alm_block(int bx, int by, const float* __restrict__ c,
                                           const float* __restrict__ c_prev,
@@ -361,34 +420,42 @@ __device__ __forceinline__ void alm_block(int bx, int by, const float* __restric
   const int C = nch<CT>(g);
   const int r = by * kTvBY + threadIdx.y;
   float a_r2 = 0.0f, a_s2 = 0.0f, a_dc2 = 0.0f, a_cn2 = 0.0f, a_K = 0.0f;
-  const double gam = g.gamma, inv2hx = (double)g.inv2hx, inv2hy = (double)g.inv2hy;
+  const double gam = g.gamma;
   if (r < g.H) {
+    // the gradient along an axis vanishes on its first and last index (and on sides of
+    // length 1 or 2): there k = 0 and the neighbours are the pixel itself
+    const bool yin = r >= 1 && r <= g.H - 2;
+    const float ky = yin ? g.inv2hy : 0.0f;
+    const int up = yin ? g.W : 0;
 #pragma unroll
     for (int i = 0; i < kPPT; ++i) {
       const int q = bx * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
       if (q >= g.W) break;
+      const bool xin = q >= 1 && q <= g.W - 2;
+      const float kx = xin ? g.inv2hx : 0.0f;
+      const int rt = xin ? 1 : 0;
       const size_t k = (size_t)r * g.W + q;
+      const float* ck = c + k * C;
       const float* vk = v + k * 2 * C;
       float* mk = mu + k * 2 * C;
       float gg2 = 0.0f, tvs = 0.0f, fid = 0.0f;
       for (int ch = 0; ch < C; ++ch) {
-        const double gxd = grad_x_f64(c, g, r, q, C, ch, inv2hx);
-        const double gyd = grad_y_f64(c, g, r, q, C, ch, inv2hy);
-        const float vx = __ldg(vk + ch), vy = __ldg(vk + C + ch);
-        const double dxd = widen(vx) - gxd, dyd = widen(vy) - gyd;
-        mk[ch] = narrow(fma(gam, dxd, widen(mk[ch])));
-        mk[C + ch] = narrow(fma(gam, dyd, widen(mk[C + ch])));
-        const float gx = narrow(gxd), gy = narrow(gyd);
-        const float rx = narrow(dxd), ry = narrow(dyd);
-        a_r2 = fmaf(rx, rx, fmaf(ry, ry, a_r2));
-        if (g.tv_mode == 0) gg2 = fmaf(gx, gx, fmaf(gy, gy, gg2));
-        else tvs += sqrtf(fmaf(gx, gx, gy * gy));
-        const float ck = __ldg(c + k * C + ch);
-        const float e = ck - __ldg(c0 + k * C + ch);
+        const ResidualPair rx = residual_pair(__ldg(vk + ch), __ldg(ck + rt * C + ch),
+                                              __ldg(ck - rt * C + ch), kx);
+        const ResidualPair ry = residual_pair(__ldg(vk + C + ch),
+                                              __ldg(ck + (size_t)up * C + ch),
+                                              __ldg(ck - (size_t)up * C + ch), ky);
+        mk[ch] = mu_update(mk[ch], rx, gam);
+        mk[C + ch] = mu_update(mk[C + ch], ry, gam);
+        a_r2 = fmaf(rx.s, rx.s, fmaf(ry.s, ry.s, a_r2));
+        if (g.tv_mode == 0) gg2 = fmaf(rx.g, rx.g, fmaf(ry.g, ry.g, gg2));
+        else tvs += sqrtf(fmaf(rx.g, rx.g, ry.g * ry.g));
+        const float cc = __ldg(ck + ch);
+        const float e = cc - __ldg(c0 + k * C + ch);
         fid = fmaf(e, e, fid);
-        a_cn2 = fmaf(ck, ck, a_cn2);
+        a_cn2 = fmaf(cc, cc, a_cn2);
         if (c_prev) {
-          const float dc = ck - __ldg(c_prev + k * C + ch);
+          const float dc = cc - __ldg(c_prev + k * C + ch);
           a_dc2 = fmaf(dc, dc, a_dc2);
         }
         if (v_prev) {
@@ -421,17 +488,15 @@ __device__ __forceinline__ void alm_block(int bx, int by, const float* __restric
 }
 
 template <int CT>
-__global__ void __launch_bounds__(kTvBX * kTvBY)
+__global__ void __launch_bounds__(kTvBX * kTvBY, 4)
 alm_kernel(const float* __restrict__ c, const float* __restrict__ c_prev,
            const float* __restrict__ c0, const float* __restrict__ v,
            const float* __restrict__ v_prev, float* __restrict__ mu, double* __restrict__ partial,
            TvGeom g) {
   float a[5];
   alm_block<CT>(blockIdx.x, blockIdx.y, c, c_prev, c0, v, v_prev, mu, g, a);
-  __shared__ double red[5 * 32];
-  double vals[5] = {(double)a[0], (double)a[1], (double)a[2], (double)a[3], (double)a[4]};
   double tot[5];
-  block_sum<5>(vals, red, tot);
+  block_sum_staged<5, kTvBX * kTvBY>(a, tot);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
@@ -529,19 +594,17 @@ pd_tv_batch_kernel(const BatchTvArgs* __restrict__ args, const BatchJob* __restr
 }
 
 template <int CT>
-__global__ void __launch_bounds__(kTvBX * kTvBY)
+__global__ void __launch_bounds__(kTvBX * kTvBY, 4)
 alm_batch_kernel(const BatchTvArgs* __restrict__ args, const BatchJob* __restrict__ jobs,
                  int njobs, const int* __restrict__ active) {
-  __shared__ double red[5 * 32];
   for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
     const BatchJob job = jobs[j];
     if (!active[job.img]) continue;
     const BatchTvArgs& a = args[job.img];
     float o[5];
     alm_block<CT>(job.tx, job.ty, a.c, a.c_prev, a.c0, a.v, a.v_prev, a.mu_io, a.g, o);
-    double vals[5] = {(double)o[0], (double)o[1], (double)o[2], (double)o[3], (double)o[4]};
     double tot[5];
-    block_sum<5>(vals, red, tot);
+    block_sum_staged<5, kTvBX * kTvBY>(o, tot);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       const size_t b = (size_t)job.ty * a.tiles_x + job.tx;
 #pragma unroll

@@ -112,13 +112,17 @@ ORACLE_CASES = [  # (H, W, C, R, regions, seed)
 ]
 
 
-@pytest.mark.parametrize("alpha,autotune", [(10.0, True), (300.0, False)])
+@pytest.mark.parametrize("alpha,autotune", [(10.0, True), (30.0, False)])
 def test_batch_matches_oracle(alpha, autotune):
     """Every image of the batch within the 64 x 64 parity workload's tolerances of the
     oracle's Algorithm 2 started from the same control (eps = 8, where the 31-band colours
     interact): colours 1e-4 max-abs, control 1e-3 relative, multiplier 1e-4.  At
     alpha = 10 the solves smooth the images (the control goes to the lower bound of E);
-    at alpha = 300 they mostly keep them."""
+    at alpha = 30 one RGB image is kept.  Both settings keep every accepted Armijo step's
+    relative decrease of L~ above 1e-5 (in the oracle's run), far above float32
+    resolution; at alpha = 100-300 the grey image's eps-step crawls with decreases near
+    4e-9, where float32 rounding of L~ can flip a decision (as at alpha = 3000 on the
+    64 x 64 workload), so those settings test the regime, not the batch."""
     ensure_lib()
     imgs = [_image(H, W, C, K, seed) for H, W, C, R, K, seed in ORACLE_CASES]
     o = _opts(k_out=3, k_in=4)
