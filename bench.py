@@ -479,7 +479,9 @@ def warm_start_eval(torch, lib, dev, count: int, size: int, seed: int = 4242,
     multiplier steps, stop at res < 1e-4.  Each image is solved on its own with solve()
     from the plain start (mu = 0, eps = 57) and with warm_solve() from the committed
     network's mu(0) and eps(0) (inference included in its time; it falls back to the
-    plain start if the warm solve diverges).  Host wall clock around each call (solve()
+    plain start, and its time includes that solve, when the warm solve diverges or ends
+    without reaching the tolerance: the plain method judges the answer).  Host wall clock
+    around each call (solve()
     synchronises with its stream).  Time to tolerance is summed over the images that
     reach 1e-4 in both arms; images that hit the multiplier-step cap are counted apart.
     The answer each arm converges to is compared: max and mean |c_warm - c_plain| per
@@ -508,7 +510,8 @@ def warm_start_eval(torch, lib, dev, count: int, size: int, seed: int = 4242,
             torch.cuda.synchronize()
             tc = time.perf_counter() - t0
             t0 = time.perf_counter()
-            iw, eps_w, _, fb = warm_solve(ctx.handle, net, img, o, c_out=c_warm)
+            iw, eps_w, _, fb = warm_solve(ctx.handle, net, img, o, c_out=c_warm,
+                                          fallback_on_miss=True)
             torch.cuda.synchronize()
             tw = time.perf_counter() - t0
             d = (c_warm - c_cold).abs()

@@ -3,9 +3,12 @@
 // shared memory as one record holding all its channels (and, for the adjoint, the adjoint
 // state after them), then the validity flag, padded to a stride that keeps vector loads of
 // consecutive cells conflict-free.  A neighbour's record is read with 8-byte (forward) or
-// 16-byte (adjoint) loads and the channel loop is unrolled in registers.  Tiles are staged
-// with asynchronous copies (cp.async) from flat, coalesced NHWC row segments; results are
-// staged back through shared memory and stored the same way.  Tile height: see wide_by.
+// 16-byte (adjoint) loads and the channel loop is unrolled in registers.  The window rows
+// stream through a ring of TH + 1 tile rows in shared memory (wide_stream): the copies of
+// the row the next window-row step adds (cp.async from flat, coalesced NHWC row segments)
+// overlap the current step's arithmetic, and the ring is small enough for two blocks per
+// SM where the whole tile with its halo allowed one.  Results are staged back through
+// shared memory and stored as flat rows.  Tile height: see wide_by.
 #pragma once
 
 #include "sweep.cuh"
@@ -15,16 +18,16 @@ namespace agents {
 constexpr int kWideBX = 32, kWideBY = 4;
 constexpr int kWideC = 31;          // the channel count with a wide instantiation
 
-// R <= 7: the adjoint's two fields and validity plane of a 32 x 4 tile with an R = 8 halo
-// would need 242 KB of shared memory (227 KB per block at most).
+// R <= 7 (the ring of an R = 8 tile would still fit; R = 8 is left to the generic kernel).
 inline bool wide_shape(int R, int C) { return R >= 1 && R <= 7 && C == kWideC; }
 
-// Tile height: 8 rows where both fields of the adjoint's tile fit (R <= 5: 206 KB of
-// shared memory at R = 5), else 4.  Taller tiles load fewer halo cells per output pixel
-// and run twice the warps per block.
+// Tile height: 4 rows (128 threads).  The adjoint holds about 200 registers per thread
+// (a pixel's 31 values, 31 adjoints and 31 sums, and a neighbour's record), so two blocks
+// of 128 threads fit an SM's registers where one of 256 did; the row ring keeps both
+// blocks' shared memory (57 KB each at R = 5) in the SM's 228 KB.
 template <int R>
-constexpr int wide_by() { return R <= 5 ? 8 : kWideBY; }
-inline int wide_tile_h(int R) { return R <= 5 ? 8 : kWideBY; }
+constexpr int wide_by() { return kWideBY; }
+inline int wide_tile_h(int) { return kWideBY; }
 
 // Record stride (floats) of a cell holding `raw` values: forward records are read with
 // 8-byte loads (stride/2 odd: 16 consecutive cells hit distinct banks), adjoint records
@@ -38,56 +41,98 @@ struct Wide {
   static constexpr int SW = TW + 2 * R, SH = TH + 2 * R, CELLS = SW * SH;
   static constexpr int REC1 = wide_rec2(C + 1);       // forward: C values, flag
   static constexpr int REC2 = wide_rec4(2 * C + 1);   // adjoint: C values, C adjoints, flag
+  // The window rows stream through a ring of NR = TH + 1 tile rows (see wide_ring_row):
+  // the rows one window-row step needs plus the one being fetched for the next step.
+  static constexpr int NR = TH + 1;
   static constexpr size_t smem(int nf) {
-    return (size_t)CELLS * (nf == 1 ? REC1 : REC2) * sizeof(float);
+    const size_t ring = (size_t)NR * SW * (nf == 1 ? REC1 : REC2) * sizeof(float);
+    const size_t stage = (size_t)TW * TH * C * sizeof(float);   // wide_store
+    return ring > stage ? ring : stage;
   }
 };
 
 // 4-byte asynchronous copy global -> shared: a thread issues all its copies of a tile
-// without waiting on each load, and waits once (wide_load_wait).
+// without waiting on each load; a row's copies are committed as one group.
 __device__ __forceinline__ void wide_cp_async4(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 
-// Stage NF fields (NHWC, C channels) of the tile at (x0, y0) plus its halo into cell
-// records: values of field f, channel ch at slot f * C + ch, the validity flag at slot
-// NF * C.  Cells outside the image hold 0; the flag is written only when the halo leaves
-// the image (interior tiles never read it).
+// The tile's window rows are streamed: row i (0 <= i < TH + 2R, image row y0 - R + i) of
+// the tile plus its halo is staged into ring slot i % NR as cell records -- values of
+// field f, channel ch at slot f * C + ch, the validity flag at slot NF * C -- with
+// asynchronous copies from the flat, coalesced NHWC row segment.  Cells outside the image
+// hold 0; the flag is written only for tiles whose halo leaves the image (interior tiles
+// never read it).  The caller commits the copies as one group per row.
 template <class T, int R, int C, int NF>
-__device__ __forceinline__ bool wide_load(float* __restrict__ sm, const float* __restrict__ f0,
-                                          const float* __restrict__ f1, const SweepGeom& g,
-                                          int x0, int y0) {
+__device__ __forceinline__ void wide_ring_row(float* __restrict__ ring,
+                                              const float* __restrict__ f0,
+                                              const float* __restrict__ f1, const SweepGeom& g,
+                                              int x0, int y0, int i, bool border) {
   constexpr int REC = NF == 1 ? T::REC1 : T::REC2;
-  const bool border = (x0 - R < 0) || (y0 - R < 0) || (x0 + T::TW + R > g.W) ||
-                      (y0 + T::TH + R > g.H);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int gx0 = x0 - R;
   const int xa = max(0, -gx0), xb = min(T::SW, g.W - gx0);   // valid columns [xa, xb)
-  for (int yy = 0; yy < T::SH; ++yy) {
-    const int gy = y0 - R + yy;
-    const bool rowok = gy >= 0 && gy < g.H;
-    const int nval = (rowok && xb > xa) ? (xb - xa) * C : 0;
-    const size_t base = rowok ? ((size_t)gy * g.W + (gx0 + xa)) * C : 0;
-    float* row = sm + (size_t)(yy * T::SW + xa) * REC;
-    for (int f = tid; f < nval; f += T::NT) {
-      const int px = f / C, ch = f - px * C;
-      wide_cp_async4(row + px * REC + ch, f0 + base + f);
-      if constexpr (NF == 2) wide_cp_async4(row + px * REC + C + ch, f1 + base + f);
-    }
+  const int gy = y0 - R + i;
+  const bool rowok = gy >= 0 && gy < g.H;
+  float* slot = ring + (size_t)(i % T::NR) * T::SW * REC;
+  const int nval = (rowok && xb > xa) ? (xb - xa) * C : 0;
+  const size_t base = rowok ? ((size_t)gy * g.W + (gx0 + xa)) * C : 0;
+  float* row = slot + (size_t)xa * REC;
+  for (int f = tid; f < nval; f += T::NT) {
+    const int px = f / C, ch = f - px * C;
+    wide_cp_async4(row + px * REC + ch, f0 + base + f);
+    if constexpr (NF == 2) wide_cp_async4(row + px * REC + C + ch, f1 + base + f);
+  }
+  if (border) {
     for (int xx = tid; xx < T::SW; xx += T::NT) {
       const bool ok = rowok && xx >= xa && xx < xb;
-      float* cell = sm + (size_t)(yy * T::SW + xx) * REC;
+      float* cell = slot + (size_t)xx * REC;
       if (!ok) {
 #pragma unroll 4
         for (int k = 0; k < NF * C; ++k) cell[k] = 0.0f;
       }
-      if (border) cell[NF * C] = ok ? 1.0f : 0.0f;
+      cell[NF * C] = ok ? 1.0f : 0.0f;
     }
   }
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-  __syncthreads();
-  return border;
+}
+
+__device__ __forceinline__ void wide_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// All committed groups but the most recent one have landed (this thread's copies).
+__device__ __forceinline__ void wide_wait_prev() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+template <class T, int R>
+__device__ __forceinline__ bool wide_border(const SweepGeom& g, int x0, int y0) {
+  return (x0 - R < 0) || (y0 - R < 0) || (x0 + T::TW + R > g.W) || (y0 + T::TH + R > g.H);
+}
+
+// Drive the window-row loop of one tile: rows 0 .. TH-1 are fetched up front; before the
+// step of window row dy the row the next step adds is fetched, so its copies overlap this
+// step's arithmetic; step(dy, slot) then runs with every row it reads in the ring (slot:
+// ring row of this thread's window row).  Barriers keep a slot from being refilled while
+// a thread still reads it.
+template <class T, int R, int C, int NF, class Step>
+__device__ __forceinline__ void wide_stream(float* __restrict__ ring, const float* __restrict__ f0,
+                                            const float* __restrict__ f1, const SweepGeom& g,
+                                            int x0, int y0, bool border, Step&& step) {
+  constexpr int NROWS = T::TH + 2 * R;
+  for (int i = 0; i < T::TH; ++i) wide_ring_row<T, R, C, NF>(ring, f0, f1, g, x0, y0, i, border);
+  wide_commit();
+#pragma unroll 1
+  for (int dy = -R; dy <= R; ++dy) {
+    const int inext = dy + R + T::TH;                  // the row step dy + 1 adds
+    if (inext < NROWS) wide_ring_row<T, R, C, NF>(ring, f0, f1, g, x0, y0, inext, border);
+    wide_commit();                                     // (possibly empty) group per step
+    wide_wait_prev();
+    __syncthreads();
+    step(dy, (dy + R + (int)threadIdx.y) % T::NR);
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 // Write the tile's results (val[C] per thread) to out (NHWC) through shared memory, so
@@ -112,26 +157,36 @@ __device__ __forceinline__ void wide_store(float* __restrict__ stage, const floa
   }
 }
 
-// Forward step of the pixel at (x0 + tx, y0 + ty): c + dt/M sum_j phi(r_kj) (c_j - c_k).
-template <class T, int R, int C, bool BORDER>
-__device__ __forceinline__ void wide_forward_body(float* __restrict__ sm, float* __restrict__ out,
-                                                  const SweepGeom& g, float kx, float ky,
-                                                  float kc, int x0, int y0) {
-  constexpr int REC = T::REC1, NV = REC / 2;
-  const int cen = (threadIdx.y + R) * T::SW + threadIdx.x + R;
-  float ci[C], acc[C];
+// The thread's own pixel: its C values of field f (0 outside the image, like the zero-filled
+// records), and whether it lies in the image.
+template <int C>
+__device__ __forceinline__ bool wide_own(const float* __restrict__ f, const SweepGeom& g, int x0,
+                                         int y0, float (&val)[C]) {
+  const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
+  const bool in = gx < g.W && gy < g.H;
+  const float* src = f + ((size_t)(in ? gy : 0) * g.W + (in ? gx : 0)) * C;
 #pragma unroll
-  for (int ch = 0; ch < C; ++ch) {
-    ci[ch] = sm[cen * REC + ch];
-    acc[ch] = 0.0f;
-  }
-#pragma unroll 1
-  for (int dy = -R; dy <= R; ++dy) {
+  for (int ch = 0; ch < C; ++ch) val[ch] = in ? __ldg(src + ch) : 0.0f;
+  return in;
+}
+
+// Forward step of the pixel at (x0 + tx, y0 + ty): c + dt/M sum_j phi(r_kj) (c_j - c_k),
+// the window rows streamed through the ring (wide_stream).
+template <class T, int R, int C, bool BORDER>
+__device__ __forceinline__ void wide_forward_tile(float* __restrict__ sm, const float* __restrict__ src,
+                                                  float* __restrict__ out, const SweepGeom& g,
+                                                  float kx, float ky, float kc, int x0, int y0) {
+  constexpr int REC = T::REC1, NV = REC / 2;
+  float ci[C], acc[C];
+  wide_own<C>(src, g, x0, y0, ci);
+#pragma unroll
+  for (int ch = 0; ch < C; ++ch) acc[ch] = 0.0f;
+  wide_stream<T, R, C, 1>(sm, src, nullptr, g, x0, y0, BORDER, [&](int dy, int slot) {
     const float sy = fmaf(-ky, (float)(dy * dy), 1.0f);
+    const int base = slot * T::SW + threadIdx.x + R;
 #pragma unroll 1
     for (int dx = -R; dx <= R; ++dx) {
-      const int e = cen + dy * T::SW + dx;
-      const float2* rec = reinterpret_cast<const float2*>(sm + e * REC);
+      const float2* rec = reinterpret_cast<const float2*>(sm + (base + dx) * REC);
       float v[2 * NV];
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
@@ -154,7 +209,7 @@ __device__ __forceinline__ void wide_forward_body(float* __restrict__ sm, float*
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) acc[ch] = fmaf(ph, d[ch], acc[ch]);
     }
-  }
+  });
 #pragma unroll
   for (int ch = 0; ch < C; ++ch) acc[ch] = fmaf(g.scale, acc[ch], ci[ch]);
   wide_store<T, C>(sm, acc, out, g, x0, y0);
@@ -163,29 +218,27 @@ __device__ __forceinline__ void wide_forward_body(float* __restrict__ sm, float*
 // Adjoint step (gather form, as adjoint_body): lam_k + dt/M sum_j [phi' eps_c delta
 // (delta . dlam) + phi dlam]; the block's D partial sums go to partial[0..1].
 template <class T, int R, int C, bool BORDER>
-__device__ __forceinline__ void wide_adjoint_body(float* __restrict__ sm, float* __restrict__ out,
+__device__ __forceinline__ void wide_adjoint_tile(float* __restrict__ sm, const float* __restrict__ c,
+                                                  const float* __restrict__ lam,
+                                                  float* __restrict__ out,
                                                   double* __restrict__ partial, const SweepGeom& g,
                                                   float kx, float ky, float kc, float ec, int x0,
                                                   int y0) {
   constexpr int REC = T::REC2, NV = REC / 4;
-  const int cen = (threadIdx.y + R) * T::SW + threadIdx.x + R;
   float ck[C], lk[C], acc[C];
+  const bool own = wide_own<C>(c, g, x0, y0, ck);
+  wide_own<C>(lam, g, x0, y0, lk);
 #pragma unroll
-  for (int ch = 0; ch < C; ++ch) {
-    ck[ch] = sm[cen * REC + ch];
-    lk[ch] = sm[cen * REC + C + ch];
-    acc[ch] = 0.0f;
-  }
+  for (int ch = 0; ch < C; ++ch) acc[ch] = 0.0f;
   const float ec20 = 20.0f * ec;
   float Dx = 0.0f, Dc = 0.0f;
-#pragma unroll 1
-  for (int dy = -R; dy <= R; ++dy) {
+  wide_stream<T, R, C, 2>(sm, c, lam, g, x0, y0, BORDER, [&](int dy, int slot) {
     const float sy = fmaf(-ky, (float)(dy * dy), 1.0f);
     const float d2y = g.inv_h2 * (float)(dy * dy);
+    const int base = slot * T::SW + threadIdx.x + R;
 #pragma unroll 1
     for (int dx = -R; dx <= R; ++dx) {
-      const int e = cen + dy * T::SW + dx;
-      const float4* rec = reinterpret_cast<const float4*>(sm + e * REC);
+      const float4* rec = reinterpret_cast<const float4*>(sm + (base + dx) * REC);
       float v[4 * NV];
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
@@ -222,18 +275,18 @@ __device__ __forceinline__ void wide_adjoint_body(float* __restrict__ sm, float*
       Dx = fmaf(gk, fmaf(g.inv_w2, (float)(dx * dx), d2y), Dx);
       Dc = fmaf(gk, s2, Dc);
     }
-  }
+  });
 #pragma unroll
   for (int ch = 0; ch < C; ++ch) acc[ch] = fmaf(g.scale, acc[ch], lk[ch]);
   if constexpr (BORDER) {
     // a pixel outside the image has zero-filled lam_k, so its paired D terms
     // (delta . lam_j) are not zero by themselves: drop them
-    if (sm[cen * REC + 2 * C] == 0.0f) Dx = Dc = 0.0f;
+    if (!own) Dx = Dc = 0.0f;
   }
   __shared__ double red[2 * 32];
-  double v[2] = {-10.0 * (double)Dx, -10.0 * (double)Dc};
+  double vv[2] = {-10.0 * (double)Dx, -10.0 * (double)Dc};
   double tot[2];
-  block_sum<2>(v, red, tot);
+  block_sum<2>(vv, red, tot);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     partial[0] = tot[0];
     partial[1] = tot[1];
@@ -250,10 +303,10 @@ wide_forward_kernel(const float* __restrict__ c, float* __restrict__ out,
   const int x0 = blockIdx.x * T::TW, y0 = blockIdx.y * T::TH;
   const float ex = (float)eps_n[0], ec = (float)eps_n[1];
   const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
-  if (wide_load<T, R, C, 1>(wsm, c, nullptr, g, x0, y0))
-    wide_forward_body<T, R, C, true>(wsm, out, g, kx, ky, kc, x0, y0);
+  if (wide_border<T, R>(g, x0, y0))
+    wide_forward_tile<T, R, C, true>(wsm, c, out, g, kx, ky, kc, x0, y0);
   else
-    wide_forward_body<T, R, C, false>(wsm, out, g, kx, ky, kc, x0, y0);
+    wide_forward_tile<T, R, C, false>(wsm, c, out, g, kx, ky, kc, x0, y0);
 }
 
 template <int R, int C>
@@ -267,10 +320,10 @@ wide_adjoint_kernel(const float* __restrict__ c, const float* __restrict__ lam,
   const float ex = (float)eps_n[0], ec = (float)eps_n[1];
   const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
   double* part = partial + 2 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x);
-  if (wide_load<T, R, C, 2>(wsm, c, lam, g, x0, y0))
-    wide_adjoint_body<T, R, C, true>(wsm, out, part, g, kx, ky, kc, ec, x0, y0);
+  if (wide_border<T, R>(g, x0, y0))
+    wide_adjoint_tile<T, R, C, true>(wsm, c, lam, out, part, g, kx, ky, kc, ec, x0, y0);
   else
-    wide_adjoint_body<T, R, C, false>(wsm, out, part, g, kx, ky, kc, ec, x0, y0);
+    wide_adjoint_tile<T, R, C, false>(wsm, c, lam, out, part, g, kx, ky, kc, ec, x0, y0);
 }
 
 // Batched (persistent) versions: step n of every (image, tile) job of the batch.
@@ -301,10 +354,10 @@ wide_forward_batch_kernel(const BatchSweepImg* __restrict__ imgs, const BatchJob
     const int x0 = job.tx * T::TW, y0 = job.ty * T::TH;
     const float ex = (float)eps_n[0], ec = (float)eps_n[1];
     const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
-    if (wide_load<T, R, C, 1>(wsm, src, nullptr, g, x0, y0))
-      wide_forward_body<T, R, C, true>(wsm, dst, g, kx, ky, kc, x0, y0);
+    if (wide_border<T, R>(g, x0, y0))
+      wide_forward_tile<T, R, C, true>(wsm, src, dst, g, kx, ky, kc, x0, y0);
     else
-      wide_forward_body<T, R, C, false>(wsm, dst, g, kx, ky, kc, x0, y0);
+      wide_forward_tile<T, R, C, false>(wsm, src, dst, g, kx, ky, kc, x0, y0);
     __syncthreads();
   }
 }
@@ -329,10 +382,11 @@ wide_adjoint_batch_kernel(const BatchSweepImg* __restrict__ imgs, const BatchJob
     const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
     const int tiles_x = (g.W + T::TW - 1) / T::TW;
     double* part = im.part_adj + ((size_t)n * im.ntiles + (size_t)job.ty * tiles_x + job.tx) * 2;
-    if (wide_load<T, R, C, 2>(wsm, batch_state(im, n), lin, g, x0, y0))
-      wide_adjoint_body<T, R, C, true>(wsm, lout, part, g, kx, ky, kc, ec, x0, y0);
+    const float* cn = batch_state(im, n);
+    if (wide_border<T, R>(g, x0, y0))
+      wide_adjoint_tile<T, R, C, true>(wsm, cn, lin, lout, part, g, kx, ky, kc, ec, x0, y0);
     else
-      wide_adjoint_body<T, R, C, false>(wsm, lout, part, g, kx, ky, kc, ec, x0, y0);
+      wide_adjoint_tile<T, R, C, false>(wsm, cn, lin, lout, part, g, kx, ky, kc, ec, x0, y0);
     __syncthreads();
   }
 }

@@ -92,3 +92,85 @@ def test_divergent_warm_start_falls_back_to_the_cold_solve():
         lib.solve(ctx.handle, o, eps0, mu0, None, c_cold)
     assert fb
     assert torch.equal(c_warm, c_cold) and torch.equal(eps, eps0) and torch.equal(mu, mu0)
+
+
+# ------------------------------------------------------------------ against the oracle
+
+def test_warm_started_solve_matches_oracle_from_the_same_start():
+    """The warm start changes only the starting point (eps(0), mu(0)) of Algorithm 2.  From
+    the network's prediction for an unseen 48 x 48 image, the GPU solve and the FP64
+    oracle's admm_solve take the same steps: colours within 1e-4 max-abs, control within
+    1e-3 relative, multiplier within 1e-4 (the plain solve's parity bar).  The oracle's
+    own cold-started run of the same image is printed beside it: the two starts can end
+    at different stationary points of the non-convex problem."""
+    ensure_lib()
+    import oracle
+    from paper_2510_16154_gb300.warmstart import WarmStartNet
+    S, k_out, k_in = 48, 2, 3
+    img_t = _images(1, S, 5151)[0].contiguous()
+    img = host(img_t).astype(np.float64)
+    net = WarmStartNet.load(WEIGHTS)
+    try:
+        mu_p, eps_p = net.predict(img_t)
+    finally:
+        net.close()
+    mu0 = mu_p.reshape(S, S, 2, 3).contiguous()
+    eps0 = eps_p.contiguous()
+    mu0_h, eps0_h = host(mu0).astype(np.float64), host(eps0)
+    p = lib.agents_default_params(S, S, 3, R, T)
+    o = lib.agents_default_solve_opts()
+    o.k_out, o.k_in = k_out, k_in
+    eps, mu = eps0.clone(), mu0.clone()
+    c = torch.empty(S, S, 3, device="cuda")
+    with lib.Context(p, img_t) as ctx:
+        info = lib.solve(ctx.handle, o, eps, mu, None, c)
+    op = oracle.Params(radius=R, nsteps=T)
+    ref = oracle.admm_solve(img, op, oracle.SolveOpts(k_out=k_out, k_in=k_in),
+                            eps0=eps0_h, mu0=mu0_h)
+    err = np.max(np.abs(host(c) - ref["c"]))
+    cold = oracle.admm_solve(img, op, oracle.SolveOpts(k_out=k_out, k_in=k_in))
+    print(f"warm GPU vs warm oracle: max|dc| {err:.2e}; warm vs cold (oracle): "
+          f"max|dc| {np.max(np.abs(ref['c'] - cold['c'])):.2e}, "
+          f"L~ {ref['outer'][-1]['Ltilde']:.4f} vs {cold['outer'][-1]['Ltilde']:.4f}")
+    assert info.trials == sum(i.trials for i in ref["inner"])
+    assert err <= 1e-4
+    assert np.max(np.abs(host(eps) - ref["eps"])) <= 1e-3 * np.max(np.abs(ref["eps"]))
+    assert np.max(np.abs(host(mu) - ref["mu"])) <= 1e-4 * max(1.0, np.max(np.abs(ref["mu"])))
+
+
+def test_warm_started_2048_result_on_a_crop_against_oracle():
+    """A 2048 x 2048 image (the evaluation size of the warm start): the colours the
+    warm-started GPU solve returns are c(T; eps*) for its final control eps*; the FP64
+    oracle integrates the same control on a crop whose centre 32 x 32 pixels lie T R = 100
+    pixels inside it (the dynamics move information at most R pixels per step, so the
+    crop's cut edges cannot reach the centre).  The crop is square and cut from a square
+    image, so the spatial spacing of the full image is kept by scaling eps_x by
+    (crop side / image side)^2.  Tolerance 1e-4 max-abs (the parity bar)."""
+    ensure_lib()
+    import oracle
+    from paper_2510_16154_gb300.warmstart import WarmStartNet, warm_solve
+    N, k_out, k_in = 2048, 2, 3
+    img_t = _images(1, N, 6161)[0].contiguous()
+    net = WarmStartNet.load(WEIGHTS)
+    o = lib.agents_default_solve_opts()
+    o.k_out, o.k_in = k_out, k_in
+    c = torch.empty(N, N, 3, device="cuda")
+    try:
+        with lib.Context(lib.agents_default_params(N, N, 3, R, T), img_t) as ctx:
+            info, eps, mu, fb = warm_solve(ctx.handle, net, img_t, o, c_out=c)
+    finally:
+        net.close()
+    assert not fb and info.outer_done == k_out
+    margin, core = T * R, 32
+    side = core + 2 * margin
+    r0, q0 = 900, 1300
+    crop = host(img_t[r0:r0 + side, q0:q0 + side]).astype(np.float64)
+    eps_crop = host(eps).copy()
+    eps_crop[:, 0] *= (side / N) ** 2
+    op = oracle.Params(radius=R, nsteps=T)
+    want = oracle.forward_final(crop, eps_crop, op)[margin:margin + core, margin:margin + core]
+    got = host(c[r0 + margin:r0 + margin + core, q0 + margin:q0 + margin + core])
+    err = np.max(np.abs(got - want))
+    print(f"2048^2 warm result, crop of {core}x{core}: max|c - oracle| {err:.2e}, "
+          f"moved {np.max(np.abs(want - crop[margin:margin + core, margin:margin + core])):.2e}")
+    assert err <= 1e-4
