@@ -231,3 +231,24 @@ def test_full_size_adjoint_step():
                                                                           57.0, 57.0, op)
     assert np.max(np.abs(lam0[rows, cols] - want)) <= 1e-5 * np.max(np.abs(lamT))
     assert obj == pytest.approx(oracle.cost_Ltilde(c1, v, mu, c0, op), rel=1e-6)
+
+
+@pytest.mark.parametrize("ec", [0.0, 1e-6, 1100.0])
+def test_adjoint_step_colour_weight_extremes(ec):
+    # the adjoint tile stages colours scaled by sqrt(eps_c / 2) (floored at 1e-8): eps_c = 0,
+    # a tiny one and the top of E, on the tiled kernels (C = 1, 3) and the wide one (C = 31)
+    ensure_lib()
+    for H, W, C, R in [(40, 70, 3, 5), (23, 67, 1, 2), (20, 40, 31, 3)]:
+        rng = np.random.default_rng(H + W + C + 1)
+        c0, v, mu, _ = _adjoint_inputs(rng, H, W, C, 2)
+        eps = np.array([[30.0, ec], [20.0, ec]])
+        p, op = params(H, W, C, R, 2, alpha=40.0, rho=0.5, gamma=0.5, eps_lo=(0.0, 0.0))
+        D, obj, lam0 = _run_adjoint(p, c0, v, mu, eps)
+        Dw, objw, lamw = _oracle_adjoint(op, c0, v, mu, eps)
+        assert np.max(np.abs(lam0 - lamw)) <= 1e-5 * np.max(np.abs(lamw))
+        assert obj == pytest.approx(objw, rel=1e-6)
+        if np.max(np.abs(Dw)) == 0.0:
+            # eps_c = 1100: every colour pair lies outside the support, nothing interacts
+            assert np.max(np.abs(D)) == 0.0 and ec > 100
+        else:
+            assert_control_derivative(D, Dw)
