@@ -39,8 +39,11 @@ template <int R, int C>
 struct Wide {
   static constexpr int TW = kWideBX, TH = wide_by<R>(), NT = kWideBX * wide_by<R>();
   static constexpr int SW = TW + 2 * R, SH = TH + 2 * R, CELLS = SW * SH;
-  static constexpr int REC1 = wide_rec2(C + 1);       // forward: C values, flag
-  static constexpr int REC2 = wide_rec4(2 * C + 1);   // adjoint: C values, C adjoints, flag
+  // Channels padded to an even count CP (pad slots hold 0), so that channel pairs are
+  // aligned float2 operands of the packed FFMA2 / FADD2 arithmetic.
+  static constexpr int CP = (C + 1) & ~1;
+  static constexpr int REC1 = wide_rec2(CP + 1);      // forward: CP values, flag
+  static constexpr int REC2 = wide_rec4(2 * CP + 1);  // adjoint: CP values, CP adjoints, flag
   // The window rows stream through a ring of NR = TH + 1 tile rows (see wide_ring_row):
   // the rows one window-row step needs plus the one being fetched for the next step.
   static constexpr int NR = TH + 1;
@@ -60,7 +63,7 @@ __device__ __forceinline__ void wide_cp_async4(float* dst, const float* src) {
 
 // The tile's window rows are streamed: row i (0 <= i < TH + 2R, image row y0 - R + i) of
 // the tile plus its halo is staged into ring slot i % NR as cell records -- values of
-// field f, channel ch at slot f * C + ch, the validity flag at slot NF * C -- with
+// field f, channel ch at slot f * CP + ch, the validity flag at slot NF * CP -- with
 // asynchronous copies from the flat, coalesced NHWC row segment.  Cells outside the image
 // hold 0; the flag is written only for tiles whose halo leaves the image (interior tiles
 // never read it).  The caller commits the copies as one group per row.
@@ -82,17 +85,21 @@ __device__ __forceinline__ void wide_ring_row(float* __restrict__ ring,
   for (int f = tid; f < nval; f += T::NT) {
     const int px = f / C, ch = f - px * C;
     wide_cp_async4(row + px * REC + ch, f0 + base + f);
-    if constexpr (NF == 2) wide_cp_async4(row + px * REC + C + ch, f1 + base + f);
+    if constexpr (NF == 2) wide_cp_async4(row + px * REC + T::CP + ch, f1 + base + f);
   }
-  if (border) {
-    for (int xx = tid; xx < T::SW; xx += T::NT) {
+  for (int xx = tid; xx < T::SW; xx += T::NT) {
+    float* cell = slot + (size_t)xx * REC;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int ch = C; ch < T::CP; ++ch) cell[f * T::CP + ch] = 0.0f;   // pad channels
+    if (border) {
       const bool ok = rowok && xx >= xa && xx < xb;
-      float* cell = slot + (size_t)xx * REC;
       if (!ok) {
 #pragma unroll 4
-        for (int k = 0; k < NF * C; ++k) cell[k] = 0.0f;
+        for (int k = 0; k < NF * T::CP; ++k) cell[k] = 0.0f;
       }
-      cell[NF * C] = ok ? 1.0f : 0.0f;
+      cell[NF * T::CP] = ok ? 1.0f : 0.0f;
     }
   }
 }
@@ -176,43 +183,44 @@ template <class T, int R, int C, bool BORDER>
 __device__ __forceinline__ void wide_forward_tile(float* __restrict__ sm, const float* __restrict__ src,
                                                   float* __restrict__ out, const SweepGeom& g,
                                                   float kx, float ky, float kc, int x0, int y0) {
-  constexpr int REC = T::REC1, NV = REC / 2;
-  float ci[C], acc[C];
+  constexpr int REC = T::REC1, NP = T::CP / 2;   // channel pairs
+  float ci[C];
   wide_own<C>(src, g, x0, y0, ci);
+  float2 nci[NP], acc[NP];
 #pragma unroll
-  for (int ch = 0; ch < C; ++ch) acc[ch] = 0.0f;
+  for (int q = 0; q < NP; ++q) {
+    nci[q] = make_float2(-ci[2 * q], 2 * q + 1 < C ? -ci[2 * q + 1] : 0.0f);
+    acc[q] = f2(0.0f);
+  }
   wide_stream<T, R, C, 1>(sm, src, nullptr, g, x0, y0, BORDER, [&](int dy, int slot) {
     const float sy = fmaf(-ky, (float)(dy * dy), 1.0f);
     const int base = slot * T::SW + threadIdx.x + R;
 #pragma unroll 1
     for (int dx = -R; dx <= R; ++dx) {
       const float2* rec = reinterpret_cast<const float2*>(sm + (base + dx) * REC);
-      float v[2 * NV];
+      float2 d[NP];
+      float2 s2a = f2(0.0f), s2b = f2(0.0f);     // four independent lanes of |d|^2
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const float2 t = rec[q];
-        v[2 * q] = t.x;
-        v[2 * q + 1] = t.y;
+      for (int q = 0; q < NP; ++q) {
+        d[q] = __fadd2_rn(rec[q], nci[q]);
+        if (q & 1) s2b = __ffma2_rn(d[q], d[q], s2b);
+        else s2a = __ffma2_rn(d[q], d[q], s2a);
       }
-      float d[C];
-      float s2p[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // four independent chains
-#pragma unroll
-      for (int ch = 0; ch < C; ++ch) {
-        d[ch] = v[ch] - ci[ch];
-        s2p[ch & 3] = fmaf(d[ch], d[ch], s2p[ch & 3]);
-      }
-      const float s2 = (s2p[0] + s2p[1]) + (s2p[2] + s2p[3]);
+      const float s2 = (s2a.x + s2b.x) + (s2a.y + s2b.y);
       const float t = fmaxf(fmaf(-kc, s2, fmaf(-kx, (float)(dx * dx), sy)), 0.0f);
       const float t2 = t * t;
       float ph = (t2 * t2) * fmaf(-4.0f, t, 5.0f);
-      if constexpr (BORDER) ph *= v[C];
+      if constexpr (BORDER) ph *= rec[NP].x;            // validity flag
+      const float2 ph2 = f2(ph);
 #pragma unroll
-      for (int ch = 0; ch < C; ++ch) acc[ch] = fmaf(ph, d[ch], acc[ch]);
+      for (int q = 0; q < NP; ++q) acc[q] = __ffma2_rn(ph2, d[q], acc[q]);
     }
   });
+  float val[C];
 #pragma unroll
-  for (int ch = 0; ch < C; ++ch) acc[ch] = fmaf(g.scale, acc[ch], ci[ch]);
-  wide_store<T, C>(sm, acc, out, g, x0, y0);
+  for (int ch = 0; ch < C; ++ch)
+    val[ch] = fmaf(g.scale, (ch & 1) ? acc[ch / 2].y : acc[ch / 2].x, ci[ch]);
+  wide_store<T, C>(sm, val, out, g, x0, y0);
 }
 
 // Adjoint step (gather form, as adjoint_body): lam_k + dt/M sum_j [phi' eps_c delta
@@ -224,12 +232,18 @@ __device__ __forceinline__ void wide_adjoint_tile(float* __restrict__ sm, const 
                                                   double* __restrict__ partial, const SweepGeom& g,
                                                   float kx, float ky, float kc, float ec, int x0,
                                                   int y0) {
-  constexpr int REC = T::REC2, NV = REC / 4;
-  float ck[C], lk[C], acc[C];
+  constexpr int REC = T::REC2, NP = T::CP / 2;
+  float ck[C], lk[C];
   const bool own = wide_own<C>(c, g, x0, y0, ck);
   wide_own<C>(lam, g, x0, y0, lk);
+  float2 nck[NP], nlk[NP], acc[NP];
 #pragma unroll
-  for (int ch = 0; ch < C; ++ch) acc[ch] = 0.0f;
+  for (int q = 0; q < NP; ++q) {
+    const bool two = 2 * q + 1 < C;
+    nck[q] = make_float2(-ck[2 * q], two ? -ck[2 * q + 1] : 0.0f);
+    nlk[q] = make_float2(-lk[2 * q], two ? -lk[2 * q + 1] : 0.0f);
+    acc[q] = f2(0.0f);
+  }
   const float ec20 = 20.0f * ec;
   float Dx = 0.0f, Dc = 0.0f;
   wide_stream<T, R, C, 2>(sm, c, lam, g, x0, y0, BORDER, [&](int dy, int slot) {
@@ -238,46 +252,42 @@ __device__ __forceinline__ void wide_adjoint_tile(float* __restrict__ sm, const 
     const int base = slot * T::SW + threadIdx.x + R;
 #pragma unroll 1
     for (int dx = -R; dx <= R; ++dx) {
-      const float4* rec = reinterpret_cast<const float4*>(sm + (base + dx) * REC);
-      float v[4 * NV];
+      const float* rec = sm + (base + dx) * REC;
+      const float4* r4 = reinterpret_cast<const float4*>(rec);
+      float2 d[NP], dl[NP];
+      float2 s2a = f2(0.0f), s2b = f2(0.0f), pa = f2(0.0f), pb = f2(0.0f);
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const float4 t = rec[q];
-        v[4 * q] = t.x;
-        v[4 * q + 1] = t.y;
-        v[4 * q + 2] = t.z;
-        v[4 * q + 3] = t.w;
+      for (int q = 0; q < NP / 2; ++q) {              // two channel pairs per 16-byte load
+        const float4 a = r4[q], b = r4[NP / 2 + q];
+        d[2 * q] = __fadd2_rn(make_float2(a.x, a.y), nck[2 * q]);
+        d[2 * q + 1] = __fadd2_rn(make_float2(a.z, a.w), nck[2 * q + 1]);
+        dl[2 * q] = __fadd2_rn(make_float2(b.x, b.y), nlk[2 * q]);
+        dl[2 * q + 1] = __fadd2_rn(make_float2(b.z, b.w), nlk[2 * q + 1]);
+        s2a = __ffma2_rn(d[2 * q], d[2 * q], s2a);
+        s2b = __ffma2_rn(d[2 * q + 1], d[2 * q + 1], s2b);
+        pa = __ffma2_rn(d[2 * q], dl[2 * q], pa);
+        pb = __ffma2_rn(d[2 * q + 1], dl[2 * q + 1], pb);
       }
-      float d[C], dl[C];
-      // each channel sum in four independent chains (latency of the FMA chains)
-      float s2p[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-      for (int ch = 0; ch < C; ++ch) {
-        d[ch] = v[ch] - ck[ch];
-        dl[ch] = v[C + ch] - lk[ch];
-        s2p[ch & 3] = fmaf(d[ch], d[ch], s2p[ch & 3]);
-        pp[ch & 3] = fmaf(d[ch], dl[ch], pp[ch & 3]);
-      }
-      const float s2 = (s2p[0] + s2p[1]) + (s2p[2] + s2p[3]);
-      const float proj = (pp[0] + pp[1]) + (pp[2] + pp[3]);
+      const float s2 = (s2a.x + s2b.x) + (s2a.y + s2b.y);
+      const float proj = (pa.x + pb.x) + (pa.y + pb.y);
       const float t = fmaxf(fmaf(-kc, s2, fmaf(-kx, (float)(dx * dx), sy)), 0.0f);
       const float t2 = t * t, t3 = t2 * t;
       float ph = (t2 * t2) * fmaf(-4.0f, t, 5.0f);
       float dph = t3 * (t - 1.0f);                       // phi' / 20
       if constexpr (BORDER) {
-        ph *= v[2 * C];
-        dph *= v[2 * C];
+        const float m = rec[2 * T::CP];                  // validity flag
+        ph *= m;
+        dph *= m;
       }
       const float gk = dph * proj;        // D in the paired form of adjoint_body
-      const float coef = gk * ec20;
+      const float2 coef = f2(gk * ec20), ph2 = f2(ph);
 #pragma unroll
-      for (int ch = 0; ch < C; ++ch) acc[ch] = fmaf(ph, dl[ch], fmaf(coef, d[ch], acc[ch]));
+      for (int q = 0; q < NP; ++q)
+        acc[q] = __ffma2_rn(ph2, dl[q], __ffma2_rn(coef, d[q], acc[q]));
       Dx = fmaf(gk, fmaf(g.inv_w2, (float)(dx * dx), d2y), Dx);
       Dc = fmaf(gk, s2, Dc);
     }
   });
-#pragma unroll
-  for (int ch = 0; ch < C; ++ch) acc[ch] = fmaf(g.scale, acc[ch], lk[ch]);
   if constexpr (BORDER) {
     // a pixel outside the image has zero-filled lam_k, so its paired D terms
     // (delta . lam_j) are not zero by themselves: drop them
@@ -291,7 +301,11 @@ __device__ __forceinline__ void wide_adjoint_tile(float* __restrict__ sm, const 
     partial[0] = tot[0];
     partial[1] = tot[1];
   }
-  wide_store<T, C>(sm, acc, out, g, x0, y0);
+  float val[C];
+#pragma unroll
+  for (int ch = 0; ch < C; ++ch)
+    val[ch] = fmaf(g.scale, (ch & 1) ? acc[ch / 2].y : acc[ch / 2].x, lk[ch]);
+  wide_store<T, C>(sm, val, out, g, x0, y0);
 }
 
 template <int R, int C>
