@@ -837,15 +837,15 @@ def main():
     peak_basis = (f"measured: FMA probe ({'FFMA2' if fp32['ffma2_tflops'] >= fp32['ffma_tflops'] else 'FFMA'}"
                   f" chains, {fp32['sms']} SMs x 8 blocks x 256 threads) at a median "
                   f"{fp32_clock} MHz SM clock")
-    # DRAM traffic: the ncu capture at 4096 x 4096 x 3 (201.35 MB read + 158.56 MB written
-    # per launch, profiles/forward_tile_kernel_4096x4096x3_R5.md) predates the kernel's
-    # pre-scaled colour tile and its re-read of the unscaled centre values at the store,
-    # so it no longer describes this kernel and is not reported.
-    traffic = None
+    # DRAM traffic per launch from one ncu capture of this kernel at this size (one pass,
+    # caches flushed: profiles/forward_tile_kernel_1024x1024x3_R5_traffic.md): the 12.6 MB
+    # input read; the 12.6 MB output stays in the 129 MB L2 within the launch.
+    traffic = 12606464          # bytes read; 0 bytes written back within the launch
     roofline = {"bound": "alu", "kernel": "forward_tile_kernel<5,3>", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_basis": "none: the kernel changed after its ncu capture (201.35 MB read "
-                                 "+ 158.56 MB written per 4096x4096x3 launch before)",
+                "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture "
+                                 "of this launch (1024x1024x3, R=5): 12.61 MB + 0 B",
+                "peak_kind": "burst: the FMA probe timed alone, like this kernel",
                 "algorithmic_bytes": 8 * C * H * W,
                 "peak_basis": peak_basis, "fp32_probe": fp32,
                 "launch_us": launch_s * 1e6,
