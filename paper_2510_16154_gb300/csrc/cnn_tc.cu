@@ -14,9 +14,10 @@
 // MMAs per row and K group, no im2col copy.  The weights of the K group are staged once
 // for all rows as 9 taps x 2 halves x NT rows of 16 bytes (the B operand, K-major); each
 // output row accumulates in its own NT columns of tensor memory.
-// Two stage buffers alternate: while the tensor core works on one K group the threads
-// stage the next; a buffer is refilled only after the tcgen05.commit of the MMAs that read
-// it has arrived on its mbarrier.  One thread issues the MMAs; the accumulators (128 lanes
+// Three stage buffers rotate: while the tensor core works on one K group the threads
+// stage the next, whose activations were fetched into registers during the group before
+// (the weights go to shared memory by 16-byte asynchronous copies); a buffer is refilled
+// only after the tcgen05.commit of the MMAs that read it has arrived on its mbarrier.  One thread issues the MMAs; the accumulators (128 lanes
 // x NT columns of float32 per row) are read back with tcgen05.ld: warp w reads lanes
 // 32 (w mod 4) .. +31 (pixels of the segment) and every other 16-column chunk, starting at
 // chunk w / 4, for the bias/ReLU/skip epilogue.
@@ -44,6 +45,10 @@ constexpr int kTcThreads = 256;
 constexpr int kPlane = kTcSlots * 16;     // bytes of one (row, 8-channel half) patch plane
 constexpr int kPatchBytes = (kRows + 2) * 2 * kPlane;
 constexpr int kHeader = 128;              // mbarriers and the TMEM address
+constexpr int kStages = 3;                // stage buffers (K groups in flight)
+// Patch items (one pixel slot of one patch row, 16 channels) and weight items (one tap and
+// output channel, 16 channels) a thread moves per K group, at most.
+constexpr int kPatchItems = ((kRows + 2) * kTcSlots + kTcThreads - 1) / kTcThreads;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 __device__ int tc_error = 0;
@@ -162,13 +167,13 @@ __global__ void __launch_bounds__(kTcThreads) tc_conv_kernel(TcArgs g) {
   const int stages = g.CI / 16;
   const int sbytes = stage_bytes(nt);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 16);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 32);
   uint8_t* stage0 = smem + kHeader;
   const uint32_t ncols = (uint32_t)tmem_cols(nt);
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[1])) : "memory");
+    for (int b = 0; b < kStages; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[b])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -185,43 +190,68 @@ __global__ void __launch_bounds__(kTcThreads) tc_conv_kernel(TcArgs g) {
   const uint32_t idesc = instr_desc(kTcM, nt);
 
   const int Hs = g.H >> g.up, Ws = g.W >> g.up;
+  const int npatch = (nrows + 2) * kTcSlots;
+  // The patch of K group s (float32 activations, converted to bfloat16 on the way into
+  // shared memory) is fetched into registers one group ahead: its loads are in flight
+  // while the tensor core multiplies the group before.  The weights (already bfloat16)
+  // go straight to shared memory with 16-byte asynchronous copies.
+  float4 pf[kPatchItems][4];
+  auto fetch_patch = [&](int s) {
+    const int c0 = s * 16;
+#pragma unroll
+    for (int k = 0; k < kPatchItems; ++k) {
+      const int it = tid + k * kTcThreads;
+      const int rr = it / kTcSlots, sl = it - rr * kTcSlots;
+      const int yy = py0 + rr - 1, xx = x0 + sl - 1;
+      if (it < npatch && yy >= 0 && yy < g.H && xx >= 0 && xx < g.W) {
+        const float4* p = reinterpret_cast<const float4*>(
+            g.x + (((size_t)img * Hs + (yy >> g.up)) * Ws + (xx >> g.up)) * g.CI + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pf[k][q] = __ldg(p + q);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pf[k][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  };
   bool ok = true;
   int issued = 0;                                    // stages whose MMAs were committed
+  if (stages > 0) fetch_patch(0);
   for (int s = 0; s < stages; ++s) {
-    const int b = s & 1;
+    const int b = s % kStages;
     uint8_t* st = stage0 + b * sbytes;
-    if (s >= 2) {
-      const bool mine = mbar_wait(smem_addr(&bars[b]), (uint32_t)(((s - 2) >> 1) & 1));
+    if (s >= kStages) {     // the MMAs that read this buffer (K group s - kStages) are done
+      const bool mine = mbar_wait(smem_addr(&bars[b]), (uint32_t)(((s - kStages) / kStages) & 1));
       if (__syncthreads_or(!mine)) { ok = false; break; }
     }
     const int c0 = s * 16;
-    // patch: nrows + 2 rows x 130 slots, 16 channels each -> two 16-byte halves
-    for (int it = tid; it < (nrows + 2) * kTcSlots; it += kTcThreads) {
-      const int rr = it / kTcSlots, sl = it - rr * kTcSlots;
-      const int yy = py0 + rr - 1, xx = x0 + sl - 1;
-      uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
-      if (yy >= 0 && yy < g.H && xx >= 0 && xx < g.W) {
-        const float* p = g.x + (((size_t)img * Hs + (yy >> g.up)) * Ws + (xx >> g.up)) * g.CI + c0;
-        const float4 a0 = __ldg(reinterpret_cast<const float4*>(p));
-        const float4 a1 = __ldg(reinterpret_cast<const float4*>(p) + 1);
-        const float4 a2 = __ldg(reinterpret_cast<const float4*>(p) + 2);
-        const float4 a3 = __ldg(reinterpret_cast<const float4*>(p) + 3);
-        lo = make_uint4(pack2(a0.x, a0.y), pack2(a0.z, a0.w), pack2(a1.x, a1.y), pack2(a1.z, a1.w));
-        hi = make_uint4(pack2(a2.x, a2.y), pack2(a2.z, a2.w), pack2(a3.x, a3.y), pack2(a3.z, a3.w));
-      }
-      *reinterpret_cast<uint4*>(st + (rr * 2 + 0) * kPlane + sl * 16) = lo;
-      *reinterpret_cast<uint4*>(st + (rr * 2 + 1) * kPlane + sl * 16) = hi;
-    }
     // weights: 9 taps x NT rows, 16 channels each -> two 16-byte halves
     uint8_t* wb = st + kPatchBytes;
     for (int it = tid; it < 9 * nt; it += kTcThreads) {
       const int tap = it / nt, n = it - tap * nt;
-      const uint4* p = reinterpret_cast<const uint4*>(g.w + ((size_t)(n0 + n) * 9 + tap) * g.CI + c0);
-      const uint4 lo = __ldg(p), hi = __ldg(p + 1);
-      *reinterpret_cast<uint4*>(wb + (tap * 2 + 0) * nt * 16 + n * 16) = lo;
-      *reinterpret_cast<uint4*>(wb + (tap * 2 + 1) * nt * 16 + n * 16) = hi;
+      const __nv_bfloat16* p = g.w + ((size_t)(n0 + n) * 9 + tap) * g.CI + c0;
+      const uint32_t d0 = smem_addr(wb + (tap * 2 + 0) * nt * 16 + n * 16);
+      const uint32_t d1 = smem_addr(wb + (tap * 2 + 1) * nt * 16 + n * 16);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d0), "l"(p) : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d1), "l"(p + 8) : "memory");
     }
-    // make the generic-proxy stores visible to the tensor core (async proxy)
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    // patch: nrows + 2 rows x 130 slots, 16 channels each -> two 16-byte halves
+#pragma unroll
+    for (int k = 0; k < kPatchItems; ++k) {
+      const int it = tid + k * kTcThreads;
+      if (it < npatch) {
+        const int rr = it / kTcSlots, sl = it - rr * kTcSlots;
+        const float4 a0 = pf[k][0], a1 = pf[k][1], a2 = pf[k][2], a3 = pf[k][3];
+        const uint4 lo = make_uint4(pack2(a0.x, a0.y), pack2(a0.z, a0.w), pack2(a1.x, a1.y), pack2(a1.z, a1.w));
+        const uint4 hi = make_uint4(pack2(a2.x, a2.y), pack2(a2.z, a2.w), pack2(a3.x, a3.y), pack2(a3.z, a3.w));
+        *reinterpret_cast<uint4*>(st + (rr * 2 + 0) * kPlane + sl * 16) = lo;
+        *reinterpret_cast<uint4*>(st + (rr * 2 + 1) * kPlane + sl * 16) = hi;
+      }
+    }
+    if (s + 1 < stages) fetch_patch(s + 1);          // in flight during this group's MMAs
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    // make the generic-proxy stores and copies visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
@@ -243,9 +273,10 @@ __global__ void __launch_bounds__(kTcThreads) tc_conv_kernel(TcArgs g) {
     }
     ++issued;
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   if (ok && issued > 0) {
     const int s = issued - 1;
-    const bool mine = mbar_wait(smem_addr(&bars[s & 1]), (uint32_t)((s >> 1) & 1));
+    const bool mine = mbar_wait(smem_addr(&bars[s % kStages]), (uint32_t)((s / kStages) & 1));
     if (__syncthreads_or(!mine)) ok = false;
   }
   fence_after_sync();
@@ -301,7 +332,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_conv_kernel(TcArgs g) {
     // accumulators' columns are released.
     if (issued > 0) {
       const int s = issued - 1;
-      mbar_wait(smem_addr(&bars[s & 1]), (uint32_t)((s >> 1) & 1));
+      mbar_wait(smem_addr(&bars[s % kStages]), (uint32_t)((s / kStages) & 1));
     }
   }
   fence_before_sync();
@@ -321,14 +352,18 @@ int tc_tile_n(int co) {
   return co % 128 == 0 ? 128 : 0;
 }
 
-// Shared memory of a CTA: header and two stage buffers.  Every address a descriptor of a
+// Shared memory of a CTA: header and min(kStages, K groups) stage buffers.  Every address a descriptor of a
 // stage reaches (the start, 15 M-stride steps and one K-stride step) lies inside that
 // stage: the last row's last tap ends exactly at the end of the patch, the last tap's
 // weights at the end of the stage.
-size_t tc_smem_bytes(int nt) { return (size_t)kHeader + 2 * (size_t)stage_bytes(nt); }
+size_t tc_smem_bytes(int nt, int kgroups) {
+  const int nbuf = kgroups < kStages ? (kgroups > 0 ? kgroups : 1) : kStages;
+  return (size_t)kHeader + nbuf * (size_t)stage_bytes(nt);
+}
 
 cudaError_t launch_tc(TcArgs g, int N, cudaStream_t s) {
-  const size_t smem = tc_smem_bytes(g.nt);
+  const size_t smem = tc_smem_bytes(g.nt, g.CI / 16);   // layers with fewer K groups than
+                                                         // kStages use fewer buffers
   static size_t configured = 0;       // dynamic shared memory the kernel is opted into
   if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
