@@ -483,7 +483,9 @@ def warm_start_eval(torch, lib, dev, count: int, size: int, seed: int = 4242,
     ramp 0.1, sigma ~ U[0.02, 0.15]) of size^2, R = 5, T = 20, k_in = 10, at most k_out
     multiplier steps, stop at res < 1e-4.  Each image is solved on its own with solve()
     from the plain start (mu = 0, eps = 57) and with warm_solve() from the committed
-    network's mu(0) and eps(0) (inference included in its time; a diverging warm solve
+    network's mu(0) and eps(0) (predicted at the training resolution 256^2 from block
+    means and upsampled for larger images; inference included in its time; a diverging
+    warm solve
     falls back to the plain start).  Host wall clock around each call (solve()
     synchronises with its stream).  Two policies are reported from the same runs:
       * "warm": the warm-started answer stands whenever the solve ends (the plain
@@ -569,17 +571,17 @@ def warm_start_eval(torch, lib, dev, count: int, size: int, seed: int = 4242,
     }
 
 
-def warmstart_workload(torch, lib, dev, count: int, size: int):
+def warmstart_workload(torch, lib, dev, count: int, size: int, k_out: int = 40):
     """The learned warm start's own line: warm_start_eval on `count` images of size^2."""
     from paper_2510_16154_gb300.train_warmstart import R as R_WS, T as T_WS
-    res = warm_start_eval(torch, lib, dev, count, size)
+    res = warm_start_eval(torch, lib, dev, count, size, k_out=k_out)
     tt = res["warm"]
     return {"metric": "time to relative residual 1e-4, warm start vs plain (images reaching "
                       "it in both arms)",
             "value": tt["time_to_tol_s"], "unit": "s", "higher_is_better": False,
             "cold_seconds": tt["plain_time_to_tol_s"], "speedup": tt["speedup"],
             "config": {"workload": f"{count} unseen {size}x{size}x3 Voronoi+ramp+noise images, "
-                                   f"R={R_WS}, T={T_WS}, k_in=10, k_out<=40, tol 1e-4, "
+                                   f"R={R_WS}, T={T_WS}, k_in=10, k_out<={k_out}, tol 1e-4, "
                                    "one solve() per image",
                        "weights": "paper_2510_16154_gb300/weights/warmstart_rgb_T20_R5.npz"},
             **res}
@@ -698,6 +700,8 @@ def main():
                     help="images of the warm-start time-to-tolerance comparison (0: skip it "
                          "in the default line)")
     ap.add_argument("--warm-size", type=int, default=256)
+    ap.add_argument("--warm-k-out", type=int, default=40,
+                    help="multiplier-step cap of the warm-start workload")
     ap.add_argument("--batch-T", type=int, default=0,
                     help="horizon of the batch workload (0: T = 20)")
     ap.add_argument("--batch-tol-outer", type=int, default=0,
@@ -737,7 +741,8 @@ def main():
             print(json.dumps(res), flush=True)
         return 0
     if args.workload == "warmstart":
-        res = warmstart_workload(torch, lib, dev, args.warm_count, args.warm_size)
+        res = warmstart_workload(torch, lib, dev, args.warm_count, args.warm_size,
+                                 args.warm_k_out)
         if rank == 0:
             print(json.dumps(res), flush=True)
         return 0

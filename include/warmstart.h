@@ -106,6 +106,16 @@ int ws_net_get_params(ws_net* net, float* params);
 int ws_net_forward(ws_net* net, const float* img, int32_t N, int32_t H, int32_t W,
                    int32_t project, float* mu_out, double* eps_out, float* z_out);
 
+/* Inference at a coarser resolution, lifted back: the f x f block means of the images
+ * (H, W multiples of factor) go through ws_net_forward at H/f x W/f, and mu_out
+ * [N][H][W][out_ch] (device) receives the prediction upsampled by nearest neighbour;
+ * eps_out as in ws_net_forward (the control lives on the unit square and does not depend
+ * on the resolution).  For images larger than those the network was trained on: the
+ * prediction is made at the training resolution.  factor = 1 is ws_net_forward.  No
+ * counterpart in the paper (its method has no network). */
+int ws_net_forward_lifted(ws_net* net, const float* img, int32_t N, int32_t H, int32_t W,
+                          int32_t factor, int32_t project, float* mu_out, double* eps_out);
+
 /* Loss  mean((mu - mu_t)^2) + lam_eps mean((z - log_eps_t)^2)  for N images whose sides
  * are multiples of 2^(levels-1), and its gradient with respect to the flat parameters.
  * mu_t [N][H][W][out_ch] float32, log_eps_t [N][2T] float32 (device).  loss_out (host,

@@ -131,6 +131,8 @@ _SIGNATURES = {
     "ws_net_get_params": (c_int, [c_void_p, c_void_p]),
     "ws_net_forward": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32,
                                c_void_p, c_void_p, c_void_p]),
+    "ws_net_forward_lifted": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32,
+                                      c_int32, c_void_p, c_void_p]),
     "ws_net_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                  c_int32, ctypes.c_float, POINTER(c_double), c_void_p]),
     "ws_net_adam_step": (c_int, [c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_float,

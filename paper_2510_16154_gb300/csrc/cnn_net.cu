@@ -257,6 +257,45 @@ __global__ void pad_kernel(const float* __restrict__ x, float* __restrict__ y, i
 
 // Crop [N][Hp][Wp][C] -> [N][H][W][C] and project each pixel's dual onto the unit ball:
 // mode 1: one ball per pixel over all C entries; mode 2: one per (x, y) channel pair.
+// f x f block means of [N][H][W][C] (H, W multiples of f) -> [N][H/f][W/f][C].
+__global__ void block_mean_kernel(const float* __restrict__ x, float* __restrict__ y, int N,
+                                  int H, int W, int C, int f) {
+  const int h = H / f, w = W / f;
+  const size_t n = (size_t)N * h * w * C;
+  const float inv = 1.0f / (float)(f * f);
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t % C);
+    size_t r = t / C;
+    const int j = (int)(r % w);
+    r /= w;
+    const int i = (int)(r % h);
+    const int b = (int)(r / h);
+    const float* src = x + (((size_t)b * H + (size_t)i * f) * W + (size_t)j * f) * C + c;
+    float acc = 0.0f;
+    for (int u = 0; u < f; ++u)
+      for (int v = 0; v < f; ++v) acc += src[((size_t)u * W + v) * C];
+    y[t] = acc * inv;
+  }
+}
+
+// Nearest upsampling by f: [N][h][w][C] -> [N][h f][w f][C].
+__global__ void upsample_nearest_kernel(const float* __restrict__ x, float* __restrict__ y,
+                                        int N, int h, int w, int C, int f) {
+  const int H = h * f, W = w * f;
+  const size_t n = (size_t)N * H * W * C;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t % C);
+    size_t r = t / C;
+    const int j = (int)(r % W);
+    r /= W;
+    const int i = (int)(r % H);
+    const int b = (int)(r / H);
+    y[t] = x[(((size_t)b * h + i / f) * w + j / f) * C + c];
+  }
+}
+
 __global__ void crop_project_kernel(const float* __restrict__ src, float* __restrict__ dst, int N,
                                     int H, int W, int Hp, int Wp, int C, int mode) {
   const size_t np = (size_t)N * H * W;
@@ -749,6 +788,41 @@ int ws_net_forward(ws_net* net, const float* img, int32_t N, int32_t H, int32_t 
   }
   if (prev >= 0 && prev != net->device) cudaSetDevice(prev);
   return AGENTS_OK;
+}
+
+int ws_net_forward_lifted(ws_net* net, const float* img, int32_t N, int32_t H, int32_t W,
+                          int32_t factor, int32_t project, float* mu_out, double* eps_out) {
+  if (!net || !img || !mu_out || N < 1 || factor < 1 || H < factor || W < factor ||
+      H % factor || W % factor)
+    return ws_fail(AGENTS_EINVAL, "ws_net_forward_lifted: bad arguments (sides must be "
+                                  "multiples of factor)");
+  if (factor == 1) return ws_net_forward(net, img, N, H, W, project, mu_out, eps_out, nullptr);
+  const int h = H / factor, w = W / factor;
+  const int ci = net->cfg.in_ch, co = net->cfg.out_ch;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != net->device) cudaSetDevice(net->device);
+  float *small = nullptr, *small_mu = nullptr;
+  WCK(cudaMallocAsync(&small, (size_t)N * h * w * ci * sizeof(float), net->stream));
+  cudaError_t e = cudaMallocAsync(&small_mu, (size_t)N * h * w * co * sizeof(float), net->stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(small, net->stream);
+    return ws_fail(AGENTS_ENOMEM, "ws_net_forward_lifted: allocation failed");
+  }
+  block_mean_kernel<<<blocks_for((size_t)N * h * w * ci), kThreads, 0, net->stream>>>(
+      img, small, N, H, W, ci, factor);
+  int st = cudaGetLastError() == cudaSuccess ? AGENTS_OK : AGENTS_ECUDA;
+  if (st == AGENTS_OK) st = ws_net_forward(net, small, N, h, w, project, small_mu, eps_out, nullptr);
+  if (st == AGENTS_OK) {
+    upsample_nearest_kernel<<<blocks_for((size_t)N * H * W * co), kThreads, 0, net->stream>>>(
+        small_mu, mu_out, N, h, w, co, factor);
+    if (cudaGetLastError() != cudaSuccess) st = AGENTS_ECUDA;
+  }
+  cudaFreeAsync(small_mu, net->stream);
+  cudaFreeAsync(small, net->stream);
+  if (prev >= 0 && prev != net->device) cudaSetDevice(prev);
+  if (st == AGENTS_ECUDA) return ws_fail(st, "ws_net_forward_lifted: kernel launch failed");
+  return st;
 }
 
 int ws_net_loss_grad(ws_net* net, const float* img, const float* mu_t, const float* log_eps_t,

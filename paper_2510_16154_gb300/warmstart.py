@@ -124,19 +124,26 @@ class WarmStartNet:
         return net
 
     # -- use
-    def predict(self, img: torch.Tensor, project: int = 1):
+    def predict(self, img: torch.Tensor, project: int = 1, lift: int = 1):
         """img [N,H,W,in_ch] or [H,W,in_ch] float32 CUDA -> (mu [..,H,W,out_ch] float32,
-        eps [..,T,2] float64), both CUDA tensors."""
+        eps [..,T,2] float64), both CUDA tensors.  lift = f > 1 predicts from the f x f
+        block means of the image and upsamples mu back (ws_net_forward_lifted): for
+        images f times the training resolution."""
         single = img.dim() == 3
         x = img.unsqueeze(0) if single else img
         x = x.contiguous()
         N, H, W, _ = x.shape
         mu = torch.empty(N, H, W, self.spec.out_ch, dtype=torch.float32, device=x.device)
         eps = torch.empty(N, self.spec.nsteps, 2, dtype=torch.float64, device=x.device)
-        lib._ws_check(lib.load().ws_net_forward(self.handle, lib._ptr(x, "float32"), N, H, W,
-                                                int(project), lib._ptr(mu, "float32"),
-                                                lib._ptr(eps, "float64"), None),
-                      "ws_net_forward")
+        if lift > 1:
+            lib._ws_check(lib.load().ws_net_forward_lifted(
+                self.handle, lib._ptr(x, "float32"), N, H, W, int(lift), int(project),
+                lib._ptr(mu, "float32"), lib._ptr(eps, "float64")), "ws_net_forward_lifted")
+        else:
+            lib._ws_check(lib.load().ws_net_forward(self.handle, lib._ptr(x, "float32"), N, H, W,
+                                                    int(project), lib._ptr(mu, "float32"),
+                                                    lib._ptr(eps, "float64"), None),
+                          "ws_net_forward")
         return (mu[0], eps[0]) if single else (mu, eps)
 
     def raw(self, img: torch.Tensor):
@@ -193,14 +200,28 @@ class WarmStartNet:
         return history
 
 
+TRAIN_SIZE = 256      # side of the images the committed weights were trained on
+
+
+def lift_factor(H: int, W: int, train_size: int = TRAIN_SIZE) -> int:
+    """The largest power of two f with H / f, W / f >= train_size dividing both sides (1 if
+    none): the factor at which the network sees an image at its training resolution."""
+    f = 1
+    while H % (2 * f) == 0 and W % (2 * f) == 0 and min(H, W) // (2 * f) >= train_size:
+        f *= 2
+    return f
+
+
 def warm_solve(ctx_handle, net: WarmStartNet, img: torch.Tensor, opts, use_eps: bool = True,
-               c_out=None, fallback_on_miss: bool = False):
+               c_out=None, fallback_on_miss: bool = False, lift: int | None = None):
     """solve() started from the network's mu(0) and eps(0) (mu only without use_eps); falls back
     to the cold start (mu = 0, eps = 57) when the warm solve diverges (AGENTS_EDIVERGED),
-    and with fallback_on_miss also when it ends without reaching opts.tol.
+    and with fallback_on_miss also when it ends without reaching opts.tol.  The prediction is
+    made at the training resolution (lift_factor) unless `lift` is given.
     Returns (info, eps, mu, used_fallback)."""
     T = net.spec.nsteps
-    mu0, eps0 = net.predict(img)
+    f = lift_factor(img.shape[0], img.shape[1]) if lift is None else lift
+    mu0, eps0 = net.predict(img, lift=f)
     eps = eps0.contiguous() if use_eps else torch.full((T, 2), 57.0, dtype=torch.float64,
                                                        device=img.device)
     mu = mu0.reshape(img.shape[0], img.shape[1], 2, -1).contiguous()
