@@ -1,7 +1,9 @@
 """CPU checks of host-side logic of the package: the warm-start network's flat parameter
 layout agrees with the oracle's for every configuration the library accepts, the
 committed weights file matches its own specification, and the high-resolution transfer
-scales the window radius as documented (round(factor R), at least 1)."""
+scales the window radius as documented (round(factor R), at least 1), and the warm
+start's lift factor brings an image to the training resolution (256) by powers of two
+that divide both sides."""
 import json
 import os
 
@@ -10,7 +12,7 @@ import pytest
 
 from oracle import cnn
 from paper_2510_16154_gb300.hires import transfer_radius
-from paper_2510_16154_gb300.warmstart import NetSpec, WEIGHTS_DIR
+from paper_2510_16154_gb300.warmstart import NetSpec, WEIGHTS_DIR, lift_factor
 
 
 @pytest.mark.parametrize("levels", [2, 3, 4, 5, 8])
@@ -42,3 +44,11 @@ def test_committed_weights_match_their_spec():
                                                 (1, 0.25, 1), (3, 1.5, 4), (7, 4.0, 28)])
 def test_transfer_radius(radius, factor, want):
     assert transfer_radius(radius, factor) == want
+
+
+@pytest.mark.parametrize("H,W,f", [(256, 256, 1), (2048, 2048, 8), (1024, 512, 2),
+                                   (2048, 1536, 4), (1100, 1100, 4), (600, 600, 2),
+                                   (64, 64, 1), (512, 768, 2)])
+def test_lift_factor(H, W, f):
+    assert lift_factor(H, W) == f
+    assert H % f == 0 and W % f == 0 and min(H, W) // f >= min(256, min(H, W))
