@@ -178,9 +178,10 @@ def test_warm_started_2048_result_on_a_crop_against_oracle():
 
 def test_lifted_prediction_is_the_coarse_prediction_upsampled():
     """ws_net_forward_lifted: the prediction for a 1024 x 1024 image made at 256 x 256 (the
-    4 x 4 block means) and upsampled by nearest neighbour equals, within float32 rounding
-    of the block means, the prediction for the block-mean image itself, repeated 4 x 4;
-    the control is the coarse image's."""
+    4 x 4 block means) and upsampled by nearest neighbour is bitwise the prediction for the
+    block-mean image itself, repeated 4 x 4 (the block means formed here in the kernel's
+    order: float32 sums over the block's rows, then its columns, times 1/16); the control
+    is the coarse image's."""
     ensure_lib()
     from paper_2510_16154_gb300.warmstart import WarmStartNet, lift_factor
     net = WarmStartNet.load(WEIGHTS)
@@ -188,14 +189,18 @@ def test_lifted_prediction_is_the_coarse_prediction_upsampled():
         img = _images(1, 1024, 8181)[0].contiguous()
         assert lift_factor(1024, 1024) == 4 and lift_factor(256, 256) == 1
         mu_l, eps_l = net.predict(img, lift=4)
-        small = img.reshape(256, 4, 256, 4, 3).mean(dim=(1, 3)).contiguous()
+        blocks = img.reshape(256, 4, 256, 4, 3)
+        acc = torch.zeros(256, 256, 3, device="cuda")
+        for u in range(4):
+            for v in range(4):
+                acc = acc + blocks[:, u, :, v]
+        small = (acc * (1.0 / 16.0)).contiguous()
         mu_s, eps_s = net.predict(small)
     finally:
         net.close()
     up = mu_s.repeat_interleave(4, dim=0).repeat_interleave(4, dim=1)
-    err = (mu_l - up).abs().max().item()
-    print(f"lifted vs coarse prediction: max |dmu| {err:.2e}")
-    assert err <= 1e-3 * max(1.0, up.abs().max().item())
-    assert torch.allclose(eps_l, eps_s, rtol=1e-4, atol=0)
+    print(f"lifted vs coarse prediction: max |dmu| {(mu_l - up).abs().max().item():.2e}")
+    assert torch.equal(mu_l, up)
+    assert torch.equal(eps_l, eps_s)
     # exactly piecewise constant on 4 x 4 blocks
     assert torch.equal(mu_l[0::4, 0::4], mu_l[3::4, 3::4])
