@@ -108,6 +108,25 @@ uint64_t agents_memory_held(void);
  * not for production use. */
 int agents_debug_set_label_loop_cap(int32_t cap);
 
+/* Test hook (no counterpart in the paper) for the whole-sweep launches.  For the tiled
+ * (R, C) a sweep of agents_forward, agents_adjoint*, agents_flow_backward, dal_solve or
+ * solve can run all its Euler (or adjoint) steps in one persistent launch: blocks take
+ * (step, tile) jobs in order and wait, each wait bounded by a time limit, until the
+ * 3 x 3 tiles around theirs have finished the previous step.  Results are bitwise those
+ * of one launch per step.
+ *   enable     0: one launch per step; 1 (the default): whole-sweep launches where they
+ *              measured faster (adjoint sweeps of images with at most 4 tiles per
+ *              resident block); 2: whole-sweep launches for every tiled sweep; other
+ *              values return AGENTS_EINVAL.
+ *   wait_ns    time limit of one wait in nanoseconds; 0 restores the default (2 s);
+ *              < 0 returns AGENTS_EINVAL.
+ *   skew_once  nonzero: the next whole-sweep launch waits for flag values that no tile
+ *              ever writes, so its first wait runs out of time; the launch then winds
+ *              down (no fault, no hang), and the API call that reads its status returns
+ *              AGENTS_ETIMEOUT and re-arms the context's flags for the calls after it.
+ * Process-wide; not for production use. */
+int agents_debug_set_fused(int32_t enable, int64_t wait_ns, uint32_t skew_once);
+
 /* Message of the last failure on ctx (or of the last failed agents_init when ctx is
  * NULL).  The string is owned by the library and valid until the next call. */
 const char* agents_last_error(const agents_ctx* ctx);

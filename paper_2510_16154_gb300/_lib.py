@@ -87,6 +87,7 @@ _SIGNATURES = {
     "agents_set_memory_limit": (c_int, [ctypes.c_uint64]),
     "agents_memory_held": (ctypes.c_uint64, []),
     "agents_debug_set_label_loop_cap": (c_int, [c_int32]),
+    "agents_debug_set_fused": (c_int, [c_int32, ctypes.c_int64, ctypes.c_uint32]),
     "agents_fp32_probe": (c_int, [c_int32, c_int32, c_int32, c_void_p, c_void_p,
                                   POINTER(c_double)]),
     "agents_last_error": (ctypes.c_char_p, [c_void_p]),
@@ -231,6 +232,14 @@ def agents_memory_held() -> int:
 
 def agents_debug_set_label_loop_cap(cap: int):
     _check(load().agents_debug_set_label_loop_cap(int(cap)), "agents_debug_set_label_loop_cap")
+
+
+def agents_debug_set_fused(mode: int = 1, wait_ns: int = 0, skew_once: int = 0):
+    """Whole-sweep launches: mode 0 never, 1 where they measured faster (default), 2 for
+    every tiled sweep; the time limit of one of their waits (0: the default); a one-shot
+    offset of the next launch's wait targets (test hook)."""
+    _check(load().agents_debug_set_fused(int(mode), int(wait_ns), int(skew_once)),
+           "agents_debug_set_fused")
 
 
 def agents_fp32_probe(packed: bool, blocks: int, iters: int, sink, stream=None) -> float:

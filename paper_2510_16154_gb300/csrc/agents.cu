@@ -60,6 +60,12 @@ namespace {
 std::atomic<uint64_t> g_mem_limit{0};
 std::atomic<uint64_t> g_mem_held{0};
 std::atomic<int32_t> g_label_loop_cap{0};
+// Whole-sweep launches (sweep_fused.cuh): 0 never, 1 where they measured faster (the
+// default), 2 for every tiled sweep; the time limit of one wait; a one-shot offset of the
+// next launch's wait targets that no flag reaches (tests of the time limit).
+std::atomic<int32_t> g_fused_enabled{1};
+std::atomic<int64_t> g_fused_wait_ns{2000000000LL};
+std::atomic<uint32_t> g_fused_skew{0};
 }  // namespace
 
 bool mem_reserve(size_t bytes) {
@@ -106,6 +112,21 @@ int agents_set_memory_limit(uint64_t bytes) {
 }
 
 uint64_t agents_memory_held(void) { return agents::g_mem_held.load(); }
+
+int agents_debug_set_fused(int32_t enable, int64_t wait_ns, uint32_t skew_once) {
+  if (wait_ns < 0) {
+    agents::set_global_error("agents_debug_set_fused: wait_ns must be >= 0");
+    return AGENTS_EINVAL;
+  }
+  if (enable < 0 || enable > 2) {
+    agents::set_global_error("agents_debug_set_fused: enable must be 0, 1 or 2");
+    return AGENTS_EINVAL;
+  }
+  agents::g_fused_enabled.store(enable);
+  agents::g_fused_wait_ns.store(wait_ns > 0 ? wait_ns : 2000000000LL);
+  agents::g_fused_skew.store(skew_once);
+  return AGENTS_OK;
+}
 
 int agents_debug_set_label_loop_cap(int32_t cap) {
   if (cap < 0) {
@@ -189,6 +210,9 @@ int to_device(agents_ctx* ctx, void* dst, const void* src, size_t n) {
   return AGENTS_OK;
 }
 
+constexpr int kStatusSlot = 15;  // d_scal slot of the whole-sweep wait status
+int fused_check(agents_ctx* ctx);
+
 // Copy n bytes from device src into dst (host or device); host destinations are
 // complete when this returns.
 int from_device(agents_ctx* ctx, void* dst, const void* src, size_t n) {
@@ -197,6 +221,7 @@ int from_device(agents_ctx* ctx, void* dst, const void* src, size_t n) {
   } else {
     CK(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    TRY(fused_check(ctx));
   }
   return AGENTS_OK;
 }
@@ -213,6 +238,99 @@ int need(agents_ctx* ctx, const void* p, const char* name) {
 }
 
 // ------------------------------------------------------------------ sweeps
+// Whole-sweep launches.  The status word of their waits is the last slot of d_scal, so
+// that every read of the small device results also reads it.
+unsigned int* fused_status_dev(agents_ctx* ctx) {
+  return reinterpret_cast<unsigned int*>(ctx->d_scal + kStatusSlot);
+}
+
+// Where whole-sweep launches pay (GB300, RGB, R = 5, T = 50): the per-SM warp scheduler
+// favours the oldest blocks, so in a persistent grid the youngest block's job lags and
+// the jobs that need its tile wait; the saving at the end of every step has to outweigh
+// that.  Measured: the adjoint of a 1024^2 image 129 vs 135 us per step (4 resident
+// blocks per SM, 3.4 tiles per block and step); 2048^2 497 vs 491 us; the forward step
+// (8 resident blocks per SM) 64.5 vs 64.3 us at 1024^2 and slower at every other size.
+// So by default only adjoint sweeps of at most 4 tiles per resident block are fused.
+constexpr int kFusedAdjointMaxTilesPerBlock = 4;
+
+bool use_fused_forward(const agents_ctx* ctx) {
+  return ctx->fused_tiles > 0 && g_fused_enabled.load() == 2;
+}
+
+bool use_fused_adjoint(const agents_ctx* ctx) {
+  const int mode = g_fused_enabled.load();
+  if (ctx->fused_tiles <= 0 || mode == 0) return false;
+  if (mode == 2) return true;
+  return (int64_t)ctx->fused_tiles <= (int64_t)kFusedAdjointMaxTilesPerBlock * ctx->fused_cap_adj;
+}
+
+FusedSync fused_sync(agents_ctx* ctx) {
+  FusedSync s = fused_sync_at(ctx->d_fsync, ctx->fused_tiles);
+  s.status = fused_status_dev(ctx);
+  s.seq0 = ctx->fused_seq;
+  s.wait_skew = g_fused_skew.exchange(0);
+  s.wait_ns = g_fused_wait_ns.load();
+  return s;
+}
+
+// Called after a synchronisation that copied d_scal[kStatusSlot] into h_scal: a fused
+// launch that gave up leaves invalid results and inconsistent flags; the flags are
+// re-armed and the call fails with AGENTS_ETIMEOUT.
+int fused_status_after_sync(agents_ctx* ctx) {
+  if (!ctx->fused_pending) return AGENTS_OK;
+  ctx->fused_pending = false;
+  unsigned int st = 0;
+  std::memcpy(&st, ctx->h_scal + kStatusSlot, sizeof(st));
+  if (st == 0) return AGENTS_OK;
+  CK(cudaMemsetAsync(ctx->d_fsync, 0, fused_sync_words(ctx->fused_tiles) * sizeof(unsigned int),
+                     ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_scal + kStatusSlot, 0, sizeof(double), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->fused_seq = 0;
+  return fail(ctx, AGENTS_ETIMEOUT,
+              "a whole-sweep launch gave up waiting for a neighbouring tile (time limit); "
+              "its results are invalid");
+}
+
+int fused_check(agents_ctx* ctx) {
+  if (!ctx->fused_pending) return AGENTS_OK;
+  CK(cudaMemcpyAsync(ctx->h_scal + kStatusSlot, ctx->d_scal + kStatusSlot, sizeof(double),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return fused_status_after_sync(ctx);
+}
+
+// Euler steps k = 0 .. n-1 from src0 under the device control d_eps (2 values per
+// step); step k writes dsts[k], which step k + 1 reads.  One launch per kFusedMaxSteps
+// steps when the tiled kernels apply, one launch per step otherwise.
+int run_forward(agents_ctx* ctx, const float* src0, const double* d_eps,
+                float* const* dsts, int n) {
+  for (int k = 0; k < n; ++k)
+    if (dsts[k] == (k == 0 ? src0 : dsts[k - 1]))
+      return fail(ctx, AGENTS_EINVAL, "an Euler step would overwrite its own input");
+  if (use_fused_forward(ctx)) {
+    for (int n0 = 0; n0 < n; n0 += kFusedMaxSteps) {
+      FusedForwardArgs a{};
+      a.src0 = n0 == 0 ? src0 : dsts[n0 - 1];
+      a.eps = d_eps + 2 * n0;
+      a.nsteps = std::min(kFusedMaxSteps, n - n0);
+      for (int k = 0; k < a.nsteps; ++k) a.dst[k] = dsts[n0 + k];
+      CK(launch_forward_fused(a, ctx->sg, fused_sync(ctx), ctx->stream));
+      ctx->fused_seq += (unsigned int)a.nsteps;
+      ctx->fused_pending = true;
+      ++ctx->launches;
+    }
+    return AGENTS_OK;
+  }
+  const float* cur = src0;
+  for (int k = 0; k < n; ++k) {
+    CK(launch_forward_step(cur, dsts[k], d_eps + 2 * k, ctx->sg, ctx->stream));
+    ++ctx->launches;
+    cur = dsts[k];
+  }
+  return AGENTS_OK;
+}
+
 // Pointer to stored state c^n (0 <= n < T) for the full-store mode.
 const float* full_state(agents_ctx* ctx, int n) {
   return n == 0 ? ctx->c0 : ctx->traj + (size_t)(n - 1) * ctx->nc;
@@ -225,6 +343,7 @@ int forward_sweep(agents_ctx* ctx, const double* d_eps, float* dst_T, bool store
   const int T = ctx->T;
   const float* cur = ctx->c0;
   int wi = 0;
+  std::vector<float*> dsts(T);
   for (int n = 0; n < T; ++n) {
     float* dst;
     if (n == T - 1) {
@@ -238,11 +357,10 @@ int forward_sweep(agents_ctx* ctx, const double* d_eps, float* dst_T, bool store
       if (dst == cur) dst = ctx->work[wi ^ 1];
       wi = (dst == ctx->work[0]) ? 1 : 0;
     }
-    CK(launch_forward_step(cur, dst, d_eps + 2 * n, ctx->sg, ctx->stream));
-    ++ctx->launches;
+    dsts[n] = dst;
     cur = dst;
   }
-  return AGENTS_OK;
+  return run_forward(ctx, ctx->c0, d_eps, dsts.data(), T);
 }
 
 // L~(c, v, mu) into d_scal[slot] (device); lam (optional) = -dL~/dc.
@@ -255,9 +373,12 @@ int objective(agents_ctx* ctx, const float* c, const float* v, const float* mu, 
 }
 
 int fetch_scalar(agents_ctx* ctx, int slot, double* out) {
-  CK(cudaMemcpyAsync(ctx->h_scal + slot, ctx->d_scal + slot, sizeof(double),
-                     cudaMemcpyDeviceToHost, ctx->stream));
+  // slot .. kStatusSlot in one copy: the status of the whole-sweep launches comes along
+  CK(cudaMemcpyAsync(ctx->h_scal + slot, ctx->d_scal + slot,
+                     (size_t)(kStatusSlot + 1 - slot) * sizeof(double), cudaMemcpyDeviceToHost,
+                     ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  TRY(fused_status_after_sync(ctx));
   *out = ctx->h_scal[slot];
   return AGENTS_OK;
 }
@@ -276,7 +397,24 @@ int adjoint_sweep_from(agents_ctx* ctx, const double* d_eps, float** lam_out) {
     li ^= 1;
     return AGENTS_OK;
   };
-  if (ctx->ckpt_every == 0) {
+  if (ctx->ckpt_every == 0 && use_fused_adjoint(ctx)) {
+    FusedAdjointArgs a{};
+    a.c0 = ctx->c0;
+    a.traj = ctx->traj;
+    a.nc = ctx->nc;
+    a.lam[0] = ctx->lam[0];
+    a.lam[1] = ctx->lam[1];
+    a.eps = d_eps;
+    a.part = ctx->d_part_adj;
+    a.pstride = pstride;
+    a.n_hi = T - 1;
+    a.n_lo = 0;
+    CK(launch_adjoint_fused(a, ctx->sg, fused_sync(ctx), ctx->stream));
+    ctx->fused_seq += (unsigned int)T;
+    ctx->fused_pending = true;
+    ++ctx->launches;
+    li = T & 1;
+  } else if (ctx->ckpt_every == 0) {
     for (int n = T - 1; n >= 0; --n) TRY(step(n, full_state(ctx, n)));
   } else {
     const int k = ctx->ckpt_every;
@@ -285,13 +423,9 @@ int adjoint_sweep_from(agents_ctx* ctx, const double* d_eps, float** lam_out) {
       const int n0 = m * k, len = std::min(k, T - n0);
       const float* base = m == 0 ? ctx->c0 : ctx->traj + (size_t)(m - 1) * ctx->nc;
       // recompute c^{n0+1} .. c^{n0+len-1} into seg[0..len-2]
-      const float* cur = base;
-      for (int i = 1; i < len; ++i) {
-        float* dst = ctx->seg + (size_t)(i - 1) * ctx->nc;
-        CK(launch_forward_step(cur, dst, d_eps + 2 * (n0 + i - 1), ctx->sg, ctx->stream));
-        ++ctx->launches;
-        cur = dst;
-      }
+      std::vector<float*> dsts(len > 1 ? len - 1 : 0);
+      for (int i = 1; i < len; ++i) dsts[i - 1] = ctx->seg + (size_t)(i - 1) * ctx->nc;
+      if (len > 1) TRY(run_forward(ctx, base, d_eps + 2 * n0, dsts.data(), len - 1));
       for (int i = len - 1; i >= 0; --i) {
         const float* cn = i == 0 ? base : ctx->seg + (size_t)(i - 1) * ctx->nc;
         TRY(step(n0 + i, cn));
@@ -324,9 +458,10 @@ int alm(agents_ctx* ctx, const float* c, const float* c_prev, const float* v,
   }
   if (h_stats) {
     double raw[5];
-    CK(cudaMemcpyAsync(ctx->h_scal + 8, ctx->d_scal + 8, 5 * sizeof(double),
+    CK(cudaMemcpyAsync(ctx->h_scal + 8, ctx->d_scal + 8, (kStatusSlot + 1 - 8) * sizeof(double),
                        cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    TRY(fused_status_after_sync(ctx));
     std::memcpy(raw, ctx->h_scal + 8, sizeof(raw));
     const double cell = ctx->tg.cell;
     h_stats[0] = std::sqrt(raw[0]);
@@ -377,14 +512,9 @@ void ensure_reuse_buffers(agents_ctx* ctx) {
 int forward_sweep_into(agents_ctx* ctx, const double* d_eps, float* traj, float* dst_T) {
   NvtxRange nr("trial_sweep");
   const int T = ctx->T;
-  const float* cur = ctx->c0;
-  for (int n = 0; n < T; ++n) {
-    float* dst = n == T - 1 ? dst_T : traj + (size_t)n * ctx->nc;
-    CK(launch_forward_step(cur, dst, d_eps + 2 * n, ctx->sg, ctx->stream));
-    ++ctx->launches;
-    cur = dst;
-  }
-  return AGENTS_OK;
+  std::vector<float*> dsts(T);
+  for (int n = 0; n < T; ++n) dsts[n] = n == T - 1 ? dst_T : traj + (size_t)n * ctx->nc;
+  return run_forward(ctx, ctx->c0, d_eps, dsts.data(), T);
 }
 
 // c(T) of the control in d_eps into dst: a copy of the stored final state when the stored
@@ -683,6 +813,10 @@ int agents_init(const agents_params* p, const float* c0, void* cuda_stream, agen
   INIT_TRY(dalloc(ctx, &ctx->d_part_adj, (size_t)T * ctx->nb_adj * 2));
   INIT_TRY(dalloc(ctx, &ctx->d_part_tv, (size_t)ctx->nb_tv * 5));
   INIT_TRY(dalloc(ctx, &ctx->d_scal, 16));
+  ctx->fused_tiles = fused_num_tiles(ctx->sg);
+  ctx->fused_cap_adj = ctx->fused_tiles > 0 ? fused_adjoint_capacity(ctx->sg) : 0;
+  if (ctx->fused_tiles > 0)
+    INIT_TRY(dalloc(ctx, &ctx->d_fsync, fused_sync_words(ctx->fused_tiles)));
   INIT_TRY(dalloc(ctx, &ctx->d_labels, (size_t)ctx->N));
   INIT_TRY(dalloc(ctx, &ctx->d_lstat, 2));
   {
@@ -698,6 +832,16 @@ int agents_init(const agents_params* p, const float* c0, void* cuda_stream, agen
                                     ctx->stream);
     if (e != cudaSuccess) {
       ctx->err = std::string("copy of the box failed: ") + cudaGetErrorString(e);
+      return bail(AGENTS_ECUDA);
+    }
+  }
+  {
+    cudaError_t e = cudaMemsetAsync(ctx->d_scal, 0, 16 * sizeof(double), ctx->stream);
+    if (e == cudaSuccess && ctx->d_fsync)
+      e = cudaMemsetAsync(ctx->d_fsync, 0,
+                          fused_sync_words(ctx->fused_tiles) * sizeof(unsigned int), ctx->stream);
+    if (e != cudaSuccess) {
+      ctx->err = std::string("clearing the sweep flags failed: ") + cudaGetErrorString(e);
       return bail(AGENTS_ECUDA);
     }
   }
@@ -741,7 +885,7 @@ int agents_forward(agents_ctx* ctx, const double* eps, float* cT_dev, int store)
     ctx->stored = false;  // cT and the work buffers were overwritten
   }
   CK(cudaStreamSynchronize(ctx->stream));  // host control buffer goes out of scope
-  return AGENTS_OK;
+  return fused_check(ctx);
 }
 
 int agents_adjoint(agents_ctx* ctx, const double* eps, const float* v_dev, const float* mu_dev,

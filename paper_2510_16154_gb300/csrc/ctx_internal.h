@@ -39,7 +39,7 @@ struct agents_ctx {
   double* d_lohi = nullptr;      // [4]
   double* d_part_adj = nullptr;  // [T][nb_adj][2]
   double* d_part_tv = nullptr;   // [nb_tv][5]
-  double* d_scal = nullptr;      // [16] small device results
+  double* d_scal = nullptr;      // [16] small device results; slot 15: sweep wait status
   double* h_scal = nullptr;      // pinned [16]
   int nb_adj = 0, nb_tv = 0;
 
@@ -64,6 +64,15 @@ struct agents_ctx {
   bool reuse = false;
   bool reuse_tried = false;
   bool traj_ok = false;
+
+  // whole-sweep launches: per-tile flags and job counters (FusedSync), the sequence
+  // number every flag holds between launches, and whether a launch has run since the
+  // last read of its status
+  unsigned int* d_fsync = nullptr;
+  int fused_tiles = 0;            // 0: no tiled kernels for (R, C), one launch per step
+  int fused_cap_adj = 0;          // resident blocks of the fused adjoint kernel
+  unsigned int fused_seq = 0;
+  bool fused_pending = false;
 
   int64_t launches = 0;           // kernels launched by this context (for accounting)
   std::vector<agents_iter_record> log;  // per-DAL-iteration records of the last solve()

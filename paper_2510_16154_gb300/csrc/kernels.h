@@ -109,6 +109,58 @@ cudaError_t launch_adjoint_step(const float* c_n, const float* lam_next, float* 
 // Number of per-block D partial pairs one adjoint step writes.
 int adjoint_num_blocks(const SweepGeom& g);
 
+// ---- whole sweeps in one launch (sweep_fused.cuh) ----
+// A persistent grid takes (step, tile) jobs in step-major order from a counter; a job of
+// step k waits until the 3 x 3 tiles around its own have finished step k - 1 (their
+// outputs are its halo, and once they have finished, nothing reads the buffer it
+// overwrites any more).  Every job whose dependencies have been taken is held by a
+// running block, so the waits always end; each is still bounded in time, after which
+// the launch gives up and records a status.  Per-tile results are bitwise those of the
+// one-launch-per-step kernels.
+struct FusedSync {
+  unsigned long long* next;  // job counter, 0 between launches
+  unsigned int* done;        // blocks that have left, 0 between launches
+  unsigned int* status;      // 0, or 1 when a wait ran out of time (sticky until reset)
+  unsigned int* flags;       // per tile: sequence number of the last completed step
+  unsigned int seq0;         // flags of every tile when the launch starts
+  unsigned int wait_skew;    // added to every wait target (0; a test sets it so that no
+                             // flag ever reaches its target)
+  long long wait_ns;         // time limit of one wait
+};
+// Words of a FusedSync block for `ntiles` tiles (one allocation, zero-initialised).
+size_t fused_sync_words(int ntiles);
+FusedSync fused_sync_at(unsigned int* base, int ntiles);
+
+constexpr int kFusedMaxSteps = 128;  // forward steps per launch (destination table size)
+struct FusedForwardArgs {
+  const float* src0;                 // state before the first step
+  const double* eps;                 // (eps_x, eps_c) of step k at eps + 2 k
+  float* dst[kFusedMaxSteps];        // output of step k; the input of step k + 1
+  int nsteps;
+};
+// Adjoint steps n = n_hi, n_hi - 1, ..., n_lo: c^n = n == 0 ? c0 : traj + (n - 1) nc; the
+// k-th step of the launch reads lam[k & 1] and writes lam[(k & 1) ^ 1]; D partials of step
+// n at part + n * pstride (tiles in row-major order).
+struct FusedAdjointArgs {
+  const float* c0;
+  const float* traj;
+  size_t nc;
+  float* lam[2];
+  const double* eps;                 // eps of step n at eps + 2 n
+  double* part;
+  size_t pstride;
+  int n_hi, n_lo;
+};
+// Tiles of the sweep kernels for (R, C); 0 when (R, C) has no tiled kernel (those sweeps
+// keep one launch per step).
+int fused_num_tiles(const SweepGeom& g);
+cudaError_t launch_forward_fused(const FusedForwardArgs& a, const SweepGeom& g,
+                                 const FusedSync& s, cudaStream_t st);
+cudaError_t launch_adjoint_fused(const FusedAdjointArgs& a, const SweepGeom& g,
+                                 const FusedSync& s, cudaStream_t st);
+// Blocks of the fused adjoint kernel resident on the whole device (0 if not tiled).
+int fused_adjoint_capacity(const SweepGeom& g);
+
 // ---- reductions (tv.cu) ----
 // out[n * nv + k] = scale * sum_b partial[(n * nblocks + b) * nv + k], for n < rows.
 cudaError_t launch_reduce_rows(const double* partial, int nblocks, int nv, int rows,

@@ -70,7 +70,16 @@ __device__ __forceinline__ float2 max0(float2 a) {
 // Stage NF fields (NHWC, C channels each) of the tile + halo into paired planar shared
 // memory, field 0 multiplied by s0.  Returns true when the halo leaves the image (the
 // validity plane is then filled with 1/0 per cell).
-template <class T, int R, int C, int NF>
+// Global loads of a sweep's inputs: through the non-coherent cache path when the data
+// was written before the launch, through L2 (COH) when another block of the same launch
+// may have written it.
+template <bool COH>
+__device__ __forceinline__ float ld_in(const float* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+
+template <class T, int R, int C, int NF, bool COH = false>
 __device__ __forceinline__ bool load_tile(float2* __restrict__ sm, float2* __restrict__ smask,
                                           const float* __restrict__ f0,
                                           const float* __restrict__ f1, const SweepGeom& g,
@@ -78,7 +87,14 @@ __device__ __forceinline__ bool load_tile(float2* __restrict__ sm, float2* __res
   const bool border = (x0 - R < 0) || (y0 - R < 0) || (x0 + T::TW + R > g.W) ||
                       (y0 + T::TH + R > g.H);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  for (int idx = tid; idx < T::PLANE; idx += T::NT) {
+  // A fixed trip count, unrolled: every load of the tile is issued before the first
+  // shared-memory store waits on one, so staging costs one global-memory latency, not
+  // one per pass.
+  constexpr int kPasses = (T::PLANE + T::NT - 1) / T::NT;
+#pragma unroll
+  for (int pass = 0; pass < kPasses; ++pass) {
+    const int idx = tid + pass * T::NT;
+    if (idx >= T::PLANE) break;
     const int yy = idx / T::SW;
     const int k = idx - yy * T::SW;
     const int gy = y0 - R + yy;
@@ -90,11 +106,11 @@ __device__ __forceinline__ bool load_tile(float2* __restrict__ sm, float2* __res
     const size_t bb = okb ? ((size_t)gy * g.W + gb) * C : 0;
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) {
-      sm[ch * T::PLANE + idx] = make_float2(oka ? s0 * __ldg(f0 + ba + ch) : 0.0f,
-                                            okb ? s0 * __ldg(f0 + bb + ch) : 0.0f);
+      sm[ch * T::PLANE + idx] = make_float2(oka ? s0 * ld_in<COH>(f0 + ba + ch) : 0.0f,
+                                            okb ? s0 * ld_in<COH>(f0 + bb + ch) : 0.0f);
       if constexpr (NF == 2)
-        sm[(C + ch) * T::PLANE + idx] = make_float2(oka ? __ldg(f1 + ba + ch) : 0.0f,
-                                                    okb ? __ldg(f1 + bb + ch) : 0.0f);
+        sm[(C + ch) * T::PLANE + idx] = make_float2(oka ? ld_in<COH>(f1 + ba + ch) : 0.0f,
+                                                    okb ? ld_in<COH>(f1 + bb + ch) : 0.0f);
     }
     if (border) smask[idx] = make_float2(oka ? 1.0f : 0.0f, okb ? 1.0f : 0.0f);
   }
@@ -132,7 +148,7 @@ __device__ __forceinline__ void store_pairs(float* __restrict__ out, const Sweep
 // and the update sum_j phi d is taken back to colour units once per pixel
 // (c^{n+1} = c^n + (dt / M) / sk * sum_j phi d, with c^n read unscaled).  Every operation
 // of an interaction is a packed pair except the clamp.
-template <class T, int C, int PXH>
+template <class T, int C, int PXH, bool COH = false>
 __device__ __forceinline__ void store_update(float* __restrict__ out,
                                              const float* __restrict__ src, const SweepGeom& g,
                                              const float2 (&acc)[PXH][C], float mult, int x0,
@@ -145,12 +161,12 @@ __device__ __forceinline__ void store_update(float* __restrict__ out,
     if (ga < g.W) {
       const size_t k = ((size_t)gy * g.W + ga) * C;
 #pragma unroll
-      for (int ch = 0; ch < C; ++ch) out[k + ch] = fmaf(mult, acc[p][ch].x, __ldg(src + k + ch));
+      for (int ch = 0; ch < C; ++ch) out[k + ch] = fmaf(mult, acc[p][ch].x, ld_in<COH>(src + k + ch));
     }
     if (gb < g.W) {
       const size_t k = ((size_t)gy * g.W + gb) * C;
 #pragma unroll
-      for (int ch = 0; ch < C; ++ch) out[k + ch] = fmaf(mult, acc[p][ch].y, __ldg(src + k + ch));
+      for (int ch = 0; ch < C; ++ch) out[k + ch] = fmaf(mult, acc[p][ch].y, ld_in<COH>(src + k + ch));
     }
   }
 }
@@ -163,7 +179,7 @@ __device__ __forceinline__ float2 max0_neg(float2 a) {
 // value (its colour term, below 1e-30 |c_j - c_i|^2, is far under float32 resolution).
 __device__ __forceinline__ float colour_scale(float kc) { return sqrtf(fmaxf(kc, 1e-30f)); }
 
-template <class T, int R, int C, int PXH, bool BORDER>
+template <class T, int R, int C, int PXH, bool BORDER, bool COH = false>
 __device__ __forceinline__ void forward_body(const float2* __restrict__ sm,
                                              const float2* __restrict__ smask,
                                              const float* __restrict__ src,
@@ -211,7 +227,7 @@ __device__ __forceinline__ void forward_body(const float2* __restrict__ sm,
       }
     }
   }
-  store_update<T, C, PXH>(out, src, g, acc, mult, x0, y0);
+  store_update<T, C, PXH, COH>(out, src, g, acc, mult, x0, y0);
 }
 
 template <int R, int C, int PXH, int BX, int BY>

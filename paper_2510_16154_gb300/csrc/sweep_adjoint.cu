@@ -1,5 +1,6 @@
 // Adjoint step launcher: tiled kernels for (R <= 8, C in {1, 3}), generic otherwise.
 #include "sweep_config.cuh"
+#include "sweep_fused.cuh"
 #include "sweep_wide.cuh"
 
 namespace agents {
@@ -80,6 +81,52 @@ int adjoint_num_blocks(const SweepGeom& g) {
   AGENTS_DISPATCH_RC(g.R, g.C, AGENTS_NB,
                      ceil_div(g.W, kGenBX) * ceil_div(g.H, untiled_tile_h(g.R, g.C)));
 #undef AGENTS_NB
+}
+
+template <int R, int C>
+static cudaError_t adjoint_fused(const FusedAdjointArgs& a, const SweepGeom& g,
+                                 const FusedSync& s, cudaStream_t st) {
+  using T = Tile<R, C, kAdjPX, kAdjBX, kAdjBY>;
+  const size_t smem = (size_t)(2 * C + 1) * T::PLANE * sizeof(float2);
+  auto kern = adjoint_fused_kernel<R, C, kAdjPX, kAdjBX, kAdjBY>;
+  static int cached = 0;
+  int grid = 0;
+  cudaError_t e = persistent_grid(kern, kAdjBX * kAdjBY, smem, &cached, &grid);
+  if (e != cudaSuccess) return e;
+  const long long jobs =
+      (long long)ceil_div(g.W, T::TW) * ceil_div(g.H, T::TH) * (a.n_hi - a.n_lo + 1);
+  if (jobs <= 0) return cudaSuccess;
+  if (jobs < grid) grid = (int)jobs;
+  kern<<<grid, dim3(kAdjBX, kAdjBY), smem, st>>>(a, g, s);
+  return cudaGetLastError();
+}
+
+template <int R, int C>
+static int adjoint_fused_capacity_rc() {
+  using T = Tile<R, C, kAdjPX, kAdjBX, kAdjBY>;
+  const size_t smem = (size_t)(2 * C + 1) * T::PLANE * sizeof(float2);
+  static int cached = 0;
+  int grid = 0;
+  if (persistent_grid(adjoint_fused_kernel<R, C, kAdjPX, kAdjBX, kAdjBY>, kAdjBX * kAdjBY, smem,
+                      &cached, &grid) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return grid;
+}
+
+int fused_adjoint_capacity(const SweepGeom& g) {
+#define AGENTS_CAP(R, C) adjoint_fused_capacity_rc<R, C>()
+  AGENTS_DISPATCH_RC(g.R, g.C, AGENTS_CAP, 0);
+#undef AGENTS_CAP
+}
+
+cudaError_t launch_adjoint_fused(const FusedAdjointArgs& a, const SweepGeom& g,
+                                 const FusedSync& s, cudaStream_t st) {
+  if (a.n_lo < 0 || a.n_hi < a.n_lo) return cudaErrorInvalidValue;
+#define AGENTS_ADJ(R, C) adjoint_fused<R, C>(a, g, s, st)
+  AGENTS_DISPATCH_RC(g.R, g.C, AGENTS_ADJ, cudaErrorInvalidValue);
+#undef AGENTS_ADJ
 }
 
 cudaError_t launch_adjoint_step(const float* c_n, const float* lam_next, float* lam_out,

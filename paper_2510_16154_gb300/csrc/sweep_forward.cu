@@ -1,5 +1,6 @@
 // Forward Euler step launcher: tiled kernels for (R <= 8, C in {1, 3}), generic otherwise.
 #include "sweep_config.cuh"
+#include "sweep_fused.cuh"
 #include "sweep_wide.cuh"
 
 namespace agents {
@@ -69,6 +70,50 @@ cudaError_t launch_forward_batch(const BatchSweepImg* imgs, const BatchJob* jobs
   AGENTS_DISPATCH_RC(R, C, AGENTS_FWD_B, cudaErrorInvalidValue);
 #undef AGENTS_FWD_B
 #undef AGENTS_FB
+}
+
+template <int R, int C>
+static cudaError_t forward_fused(const FusedForwardArgs& a, const SweepGeom& g,
+                                 const FusedSync& s, cudaStream_t st) {
+  using T = Tile<R, C, kFwdPX, kFwdBX, kFwdBY>;
+  const size_t smem = (size_t)(C + 1) * T::PLANE * sizeof(float2);
+  auto kern = forward_fused_kernel<R, C, kFwdPX, kFwdBX, kFwdBY>;
+  static int cached = 0;
+  int grid = 0;
+  cudaError_t e = persistent_grid(kern, kFwdBX * kFwdBY, smem, &cached, &grid);
+  if (e != cudaSuccess) return e;
+  const long long jobs = (long long)ceil_div(g.W, T::TW) * ceil_div(g.H, T::TH) * a.nsteps;
+  if (jobs <= 0) return cudaSuccess;
+  if (jobs < grid) grid = (int)jobs;
+  kern<<<grid, dim3(kFwdBX, kFwdBY), smem, st>>>(a, g, s);
+  return cudaGetLastError();
+}
+
+size_t fused_sync_words(int ntiles) { return 4 + (size_t)(ntiles > 0 ? ntiles : 0); }
+
+FusedSync fused_sync_at(unsigned int* base, int ntiles) {
+  (void)ntiles;
+  FusedSync s{};
+  s.next = reinterpret_cast<unsigned long long*>(base);
+  s.done = base + 2;
+  s.status = base + 3;
+  s.flags = base + 4;
+  return s;
+}
+
+int fused_num_tiles(const SweepGeom& g) {
+  if (!tiled_shape(g.R, g.C)) return 0;
+  static_assert(kFwdPX == kAdjPX && kFwdBX == kAdjBX && kFwdBY == kAdjBY,
+                "the fused sweeps share one tile grid and one set of flags");
+  return ceil_div(g.W, 2 * kFwdBX * kFwdPX) * ceil_div(g.H, kFwdBY);
+}
+
+cudaError_t launch_forward_fused(const FusedForwardArgs& a, const SweepGeom& g,
+                                 const FusedSync& s, cudaStream_t st) {
+  if (a.nsteps < 1 || a.nsteps > kFusedMaxSteps) return cudaErrorInvalidValue;
+#define AGENTS_FWD(R, C) forward_fused<R, C>(a, g, s, st)
+  AGENTS_DISPATCH_RC(g.R, g.C, AGENTS_FWD, cudaErrorInvalidValue);
+#undef AGENTS_FWD
 }
 
 cudaError_t launch_forward_step(const float* c_in, float* c_out, const double* eps_n,

@@ -488,7 +488,7 @@ __device__ __forceinline__ void alm_block(int bx, int by, const float* __restric
 }
 
 template <int CT>
-__global__ void __launch_bounds__(kTvBX * kTvBY, 4)
+__global__ void __launch_bounds__(kTvBX * kTvBY, 3)
 alm_kernel(const float* __restrict__ c, const float* __restrict__ c_prev,
            const float* __restrict__ c0, const float* __restrict__ v,
            const float* __restrict__ v_prev, float* __restrict__ mu, double* __restrict__ partial,
@@ -594,7 +594,7 @@ pd_tv_batch_kernel(const BatchTvArgs* __restrict__ args, const BatchJob* __restr
 }
 
 template <int CT>
-__global__ void __launch_bounds__(kTvBX * kTvBY, 4)
+__global__ void __launch_bounds__(kTvBX * kTvBY, 3)
 alm_batch_kernel(const BatchTvArgs* __restrict__ args, const BatchJob* __restrict__ jobs,
                  int njobs, const int* __restrict__ active) {
   for (int j = blockIdx.x; j < njobs; j += gridDim.x) {

@@ -123,3 +123,11 @@ def test_memory_limit_and_label_hook_without_a_device(cdll):
         lib.agents_debug_set_label_loop_cap(-5)
     assert e.value.code == lib.AGENTS_EINVAL
     lib.agents_debug_set_label_loop_cap(0)
+    with pytest.raises(lib.AgentsError) as e:
+        lib.agents_debug_set_fused(1, -1, 0)
+    assert e.value.code == lib.AGENTS_EINVAL
+    with pytest.raises(lib.AgentsError) as e:
+        lib.agents_debug_set_fused(5, 0, 0)
+    assert e.value.code == lib.AGENTS_EINVAL
+    lib.agents_debug_set_fused(0, 0, 0)
+    lib.agents_debug_set_fused(1, 0, 0)
