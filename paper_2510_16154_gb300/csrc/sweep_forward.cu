@@ -103,6 +103,7 @@ FusedSync fused_sync_at(unsigned int* base, int ntiles) {
 
 int fused_num_tiles(const SweepGeom& g) {
   if (!tiled_shape(g.R, g.C)) return 0;
+  if (g.R > kFwdBY || g.R > 2 * kFwdBX * kFwdPX) return 0;  // halo beyond the 3 x 3 tiles
   static_assert(kFwdPX == kAdjPX && kFwdBX == kAdjBX && kFwdBY == kAdjBY,
                 "the fused sweeps share one tile grid and one set of flags");
   return ceil_div(g.W, 2 * kFwdBX * kFwdPX) * ceil_div(g.H, kFwdBY);

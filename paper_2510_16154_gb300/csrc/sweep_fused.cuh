@@ -4,8 +4,9 @@
 // of the step run on a partly idle GPU) and starts the next with a ramp-up (every block
 // staging its tile at once); at 1024^2 that costs about a sixth of each step.  Here a
 // grid of resident blocks takes (step, tile) jobs in step-major order from one counter.
-// A job of step k needs the step-(k - 1) outputs of the 3 x 3 tiles around its own (the
-// window radius is at most the tile height, so the halo reaches no further), and waits
+// A job of step k needs the step-(k - 1) outputs of the 3 x 3 tiles around its own (used
+// only where the window radius is at most the tile height and width, so that the halo
+// reaches no further), and waits
 // for their completion flags; tiles of step k start while the last tiles of step k - 1
 // are still running.
 //
@@ -59,14 +60,18 @@ __device__ __forceinline__ bool seq_reached(unsigned int flag, unsigned int targ
 
 // Wait until *flag reaches target.  Returns false when the launch gives up: the status
 // was set by another block, or this wait ran out of time (then it sets the status).
-// Polls at most kMaxPolls times as a second bound should the timer not advance.
+// Polls at most kMaxPolls times as a second bound should the timer not advance.  The
+// pause between polls doubles from 64 ns to 1 us, so that many waiting blocks do not load
+// L2 with polls while the job they wait for still runs.
 __device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int target,
                                           unsigned int* status, long long wait_ns) {
   if (seq_reached(ld_acquire_u32(flag), target)) return true;
   constexpr int kMaxPolls = 1 << 24;
   const unsigned long long t0 = global_ns();
+  unsigned int pause = 64;
   for (int it = 0; it < kMaxPolls; ++it) {
-    __nanosleep(128);
+    __nanosleep(pause);
+    if (pause < 1024) pause *= 2;
     if (seq_reached(ld_acquire_u32(flag), target)) return true;
     if (ld_relaxed_u32(status) != 0) return false;
     if ((long long)(global_ns() - t0) > wait_ns) break;
@@ -82,7 +87,6 @@ __device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int
 template <class T, int R, class Body>
 __device__ __forceinline__ void fused_jobs(const FusedSync& s, int nsteps, const SweepGeom& g,
                                            Body body) {
-  static_assert(R <= T::TH && R <= T::TW, "the halo must stay within the 3 x 3 tiles");
   __shared__ int s_job[4];  // step, tile, tile x, tile y (step -1: no job left)
   for (;;) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -139,6 +143,9 @@ template <int R, int C, int PXH, int BX, int BY>
 __global__ void __launch_bounds__(BX * BY, 1024 / (BX * BY))
 forward_fused_kernel(const FusedForwardArgs a, SweepGeom g, FusedSync s) {
   using T = Tile<R, C, PXH, BX, BY>;
+  if constexpr (R > T::TH || R > T::TW) {
+    return;  // never launched: fused_num_tiles is 0 when the halo leaves the 3 x 3 tiles
+  } else {
   extern __shared__ __align__(16) float2 smem2[];
   float2* sm = smem2;
   float2* smask = smem2 + C * T::PLANE;
@@ -156,12 +163,16 @@ forward_fused_kernel(const FusedForwardArgs a, SweepGeom g, FusedSync s) {
     else
       forward_body<T, R, C, PXH, false, true>(sm, smask, src, dst, g, kx, ky, mult, x0, y0);
   });
+  }
 }
 
 template <int R, int C, int PXH, int BX, int BY>
 __global__ void __launch_bounds__(BX * BY, 512 / (BX * BY))
 adjoint_fused_kernel(const FusedAdjointArgs a, SweepGeom g, FusedSync s) {
   using T = Tile<R, C, PXH, BX, BY>;
+  if constexpr (R > T::TH || R > T::TW) {
+    return;  // never launched: fused_num_tiles is 0 when the halo leaves the 3 x 3 tiles
+  } else {
   extern __shared__ __align__(16) float2 smem2[];
   float2* sm = smem2;
   float2* smask = smem2 + 2 * C * T::PLANE;
@@ -182,6 +193,7 @@ adjoint_fused_kernel(const FusedAdjointArgs a, SweepGeom g, FusedSync s) {
     else
       adjoint_body<T, R, C, PXH, false>(sm, smask, lout, part, g, kx, ky, kc, ec, x0, y0);
   });
+  }
 }
 
 }  // namespace agents
