@@ -124,7 +124,9 @@ int agents_debug_set_label_loop_cap(int32_t cap);
  *              ever writes, so its first wait runs out of time; the launch then winds
  *              down (no fault, no hang), and the API call that reads its status returns
  *              AGENTS_ETIMEOUT and re-arms the context's flags for the calls after it.
- * Process-wide; not for production use. */
+ * The status is read whenever a call copies a result to the host; a call whose outputs
+ * are all device memory (agents_flow_backward without grad_eps_out) leaves it to the next
+ * call on the context that does.  Process-wide; not for production use. */
 int agents_debug_set_fused(int32_t enable, int64_t wait_ns, uint32_t skew_once);
 
 /* Message of the last failure on ctx (or of the last failed agents_init when ctx is
