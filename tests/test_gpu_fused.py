@@ -186,3 +186,51 @@ def test_wait_time_limit_reports_etimeout_and_recovers():
     with pytest.raises(lib.AgentsError) as e:
         lib.agents_debug_set_fused(3, 0, 0)
     assert e.value.code == lib.AGENTS_EINVAL
+
+
+def test_repeated_runs_are_bitwise_stable():
+    # a race between jobs (a tile staged before its neighbours' stores are visible) would
+    # show up as run-to-run differences
+    H, W, C, R, T = 256, 640, 3, 5, 8
+    img, eps = _case(H, W, C, R, T, seed=17)
+    p, _ = params(H, W, C, R, T)
+    want = _adjoint(img, eps, p, False)
+    for _ in range(10):
+        got = _adjoint(img, eps, p, True)
+        for a, b in zip(got, want):
+            assert np.array_equal(a, b)
+
+
+def test_other_stream_occupying_the_gpu():
+    # Kernels of another stream hold SMs while a whole-sweep launch runs, so not all of its
+    # persistent blocks are resident at once: jobs are still taken in order and every wait
+    # ends (a stuck wait would give up after its time limit and fail the call, not hang).
+    H, W, C, R, T = 512, 768, 3, 5, 12
+    img, eps = _case(H, W, C, R, T, seed=19)
+    p, _ = params(H, W, C, R, T)
+    want = _forward(img, eps, p, True, False)
+    Dw, ow, lw = _adjoint(img, eps, p, False)
+    busy = torch.cuda.Stream()
+    mine = torch.cuda.Stream()
+    a = torch.randn(4096, 4096, device="cuda")
+    rng = np.random.default_rng(5)
+    mu = dev(rng.normal(0.0, 0.5, (H, W, 2, C)).astype(np.float32))
+    v = dev(rng.normal(0.0, 0.2, (H, W, 2, C)).astype(np.float32))
+    torch.cuda.synchronize()
+    _fused(True)
+    cT = zeros_dev(H, W, C)
+    lam0 = zeros_dev(H, W, C)
+    D = np.zeros((T, 2))
+    obj = np.zeros(1)
+    with lib.Context(p, dev(img), mine) as ctx:
+        torch.cuda.synchronize()
+        for _ in range(3):
+            with torch.cuda.stream(busy):
+                for _ in range(4):
+                    a = torch.tanh(a @ a * 1e-4)
+            lib.agents_forward(ctx.handle, eps, cT, store=True)
+            lib.agents_adjoint(ctx.handle, eps, v, mu, D, obj, lam0)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(cT), want)
+            assert np.array_equal(D, Dw) and np.array_equal(obj, ow)
+            assert np.array_equal(host(lam0), lw)
