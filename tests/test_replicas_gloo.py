@@ -1,7 +1,8 @@
 """The N > 1 path of bench.py on CPU: two gloo ranks (replicas only: every rank solves
 its own image, the only collective is the whole-job timing).  The slowest rank's time
 and the sum of all ranks' pixel-steps give the aggregate; ranks get distinct images; the
-reference arm runs on rank 0 only."""
+reference arm runs on rank 0 only.  Also the rule by which a timed region's clock record
+disqualifies it (measured once more)."""
 import os
 import sys
 
@@ -53,3 +54,18 @@ def test_reference_arm_is_rank0_only(monkeypatch, capsys):
     monkeypatch.setattr(bench, "oracle_sample", lambda: called.append(1) or (1, 1.0))
     assert bench.run_reference(A, rank=1, world=2) == 0
     assert called == [] and capsys.readouterr().out == ""
+
+
+@pytest.mark.parametrize("clk,rejected", [
+    (None, False),
+    ({"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}, False),
+    ({"sm_mhz": 1900.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"]}, False),
+    ({"sm_mhz": 1400.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"]}, False),
+    ({"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown"]}, True),
+    ({"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_thermal_slowdown"]}, True),
+    ({"sm_mhz": 1200.0, "sm_max_mhz": 2070.0, "reasons": []}, True),   # a leftover lock
+])
+def test_clock_record_rejection(clk, rejected):
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.clocks_rejected(clk) is rejected
