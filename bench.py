@@ -622,14 +622,18 @@ def reduce_over_ranks(torch, dist, elapsed: float, pixel_steps: float, device):
 
 # ---------------------------------------------------------------- CPU oracle leg
 
-ORACLE_ROWS = 256
+ORACLE_ROWS = 256           # one step of the reference arm: a 256 x 1024 band
 ORACLE_SAMPLE = (f"top {ORACLE_ROWS} rows of the 1024x1024x3 image (R=5): one Euler step, one "
                  "adjoint step, one v-step and one multiplier update, float64 NumPy, 1 thread")
+ORACLE_BASELINE_REPS = 2    # the GPU line's baseline: the whole image, twice (about 10 s)
+ORACLE_BASELINE_SAMPLE = (f"the whole 1024x1024x3 image (R=5), {ORACLE_BASELINE_REPS} times: one "
+                          "Euler step, one adjoint step, one v-step and one multiplier update "
+                          "each, float64 NumPy, 1 thread")
 
 
-def oracle_sample():
+def oracle_sample(rows: int = ORACLE_ROWS):
     """Time the FP64 oracle on one bounded sample of the workload: one Euler step, one
-    adjoint step, one v-step and one multiplier update on a 256 x 1024 band of the image
+    adjoint step, one v-step and one multiplier update on the top `rows` rows of the image
     (the per-pixel work of the full image).  Returns (pixel-steps, seconds)."""
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
@@ -637,9 +641,9 @@ def oracle_sample():
     from oracle.tv import v_step, dual_ascent, alm_stats
     from synth import make_image, THROUGHPUT_1024_RGB
     c0 = make_image(THROUGHPUT_1024_RGB, SEED).astype(np.float32).astype(np.float64)
-    c0 = np.ascontiguousarray(c0[:ORACLE_ROWS])
+    c0 = np.ascontiguousarray(c0[:rows])
     p = oracle.Params(radius=R, nsteps=1)
-    mu = np.zeros((ORACLE_ROWS, W, 2, C))
+    mu = np.zeros((rows, W, 2, C))
     eps = np.array([[57.0, 57.0]])
     t0 = time.perf_counter()
     traj = oracle.forward(c0, eps, p)
@@ -650,7 +654,43 @@ def oracle_sample():
     alm_stats(traj[-1], v, v, c0, c0, p)
     dt = time.perf_counter() - t0
     del mu2
-    return ORACLE_ROWS * W * 4, dt
+    return rows * W * 4, dt
+
+
+def config1_solve(torch, lib, dev):
+    """The whole parity-configuration solve (64x64x3, 4 regions, noise 0.05, seed 0; R = 2,
+    T = 20, k_in = 30, k_out = 10, the paper's constants) by the FP64 oracle on one core and
+    by the library on the GPU, from the same start; wall-clock seconds of each, the steps
+    the library executed, and max |c_gpu - c_oracle| of the final colours."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    import oracle
+    from synth import make_image, PARITY_64_RGB
+    c0 = make_image(PARITY_64_RGB, 0).astype(np.float32)
+    Hc, Wc, Cc = c0.shape
+    Rc, Tc, KO, KI = 2, 20, 10, 30
+    p = lib.agents_default_params(Hc, Wc, Cc, Rc, Tc)
+    o = lib.agents_default_solve_opts()
+    o.k_out, o.k_in = KO, KI
+    eps = np.full((Tc, 2), 57.0)
+    mu = np.zeros((Hc, Wc, 2, Cc), dtype=np.float32)
+    c_gpu = np.zeros((Hc, Wc, Cc), dtype=np.float32)
+    with lib.Context(p, torch.from_numpy(c0).to(dev)) as ctx:
+        lib.solve(ctx.handle, o, eps.copy(), mu.copy(), None, c_gpu.copy(), None)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = lib.solve(ctx.handle, o, eps, mu, None, c_gpu, None)
+        gpu_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ref = oracle.admm_solve(c0.astype(np.float64), oracle.Params(radius=Rc, nsteps=Tc),
+                            oracle.SolveOpts(k_out=KO, k_in=KI))
+    oracle_s = time.perf_counter() - t0
+    return {"sample": f"{Hc}x{Wc}x{Cc}, 4 regions, noise 0.05, seed 0; R={Rc}, T={Tc}, "
+                      f"k_in={KI}, k_out={KO}; one solve from eps = 57, mu = 0",
+            "oracle_s": oracle_s, "gpu_s": gpu_s, "speedup": oracle_s / gpu_s,
+            "gpu_steps": {"forward": int(info.forward_steps), "adjoint": int(info.adjoint_steps),
+                          "tv_sweeps": int(info.tv_sweeps)},
+            "max_abs_c_diff": float(np.max(np.abs(c_gpu.astype(np.float64) - ref["c"])))}
 
 
 def cpu_cores():
@@ -926,10 +966,14 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        px, s = oracle_sample()
+        px = s = 0
+        for _ in range(ORACLE_BASELINE_REPS):
+            dpx, ds = oracle_sample(rows=H)
+            px, s = px + dpx, s + ds
         cpu = {"value": px / s / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": ORACLE_SAMPLE,
-               "host_cores": cpu_cores(), "seconds": s}
+               "sample": ORACLE_BASELINE_SAMPLE,
+               "host_cores": cpu_cores(), "seconds": s,
+               "config1_solve": config1_solve(torch, lib, dev)}
 
     ctx.close()
     if rank == 0:
