@@ -234,3 +234,24 @@ def test_other_stream_occupying_the_gpu():
             assert np.array_equal(host(cT), want)
             assert np.array_equal(D, Dw) and np.array_equal(obj, ow)
             assert np.array_equal(host(lam0), lw)
+
+
+def test_benchmark_size_default_mode_is_bitwise_the_per_step_path():
+    # at 1024^2 x 3, R = 5 the default mode runs the adjoint sweep as one launch
+    H, W, C, R, T = 1024, 1024, 3, 5, 6
+    img, eps = _case(H, W, C, R, T, seed=23)
+    p, _ = params(H, W, C, R, T)
+    ref = _adjoint(img, eps, p, False)
+    lib.agents_debug_set_fused(1, 0, 0)
+    rng = np.random.default_rng(5)
+    mu = dev(rng.normal(0.0, 0.5, (H, W, 2, C)).astype(np.float32))
+    v = dev(rng.normal(0.0, 0.2, (H, W, 2, C)).astype(np.float32))
+    D = np.zeros((T, 2))
+    obj = np.zeros(1)
+    lam0 = zeros_dev(H, W, C)
+    with lib.Context(p, dev(img)) as ctx:
+        lib.agents_forward(ctx.handle, eps, None, store=True)
+        lib.agents_adjoint(ctx.handle, eps, v, mu, D, obj, lam0)
+    assert np.array_equal(D, ref[0]) and np.array_equal(obj, ref[1])
+    assert np.array_equal(host(lam0), ref[2])
+    assert np.array_equal(_forward(img, eps, p, True, True), _forward(img, eps, p, True, False))
