@@ -343,6 +343,10 @@ cudaError_t launch_pd_tv_step(const float* c, const float* mu, float* v, const T
 // a rounding boundary, and within one float32 ulp of the exact update.
 // Per-block partial sums: |v - Gc|^2, |G^T (v - v_prev)|^2, |c - c_prev|^2, |c|^2 and
 // K(c)/(dx dy) = sum |G c_i| + alpha/2 |c_i - c0_i|^2 (float32 terms, float64 blocks).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 struct ResidualPair {
   float s, lo;  // v - k (a - b) = s + lo (to 2^-46 of the larger operand)
   float g;      // k (a - b) rounded: the gradient component for K(c)
@@ -427,6 +431,21 @@ __device__ __forceinline__ void alm_block(int bx, int by, const float* __restric
     const bool yin = r >= 1 && r <= g.H - 2;
     const float ky = yin ? g.inv2hy : 0.0f;
     const int up = yin ? g.W : 0;
+    // Ask L2 for the later pixels' lines now, so that their DRAM latency overlaps the
+    // first pixel's work (a hint: no register is written, nothing waits on it).
+#pragma unroll
+    for (int i = 1; i < kPPT; ++i) {
+      const int q = bx * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
+      if (q < g.W) {
+        const size_t k = (size_t)r * g.W + q;
+        prefetch_l2(v + k * 2 * C);
+        prefetch_l2(mu + k * 2 * C);
+        prefetch_l2(c + k * C);
+        prefetch_l2(c0 + k * C);
+        if (c_prev) prefetch_l2(c_prev + k * C);
+        if (v_prev) prefetch_l2(v_prev + k * 2 * C);
+      }
+    }
 #pragma unroll
     for (int i = 0; i < kPPT; ++i) {
       const int q = bx * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
