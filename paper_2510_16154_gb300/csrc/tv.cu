@@ -49,6 +49,32 @@ __device__ __forceinline__ float grad_y(const float* __restrict__ c, const TvGeo
 // ------------------------------------------------------------------ objective / terminal
 // Per-pixel term of L~ / (dx dy):  rho/2 |v - Gc + mu/rho|^2 + |v| + alpha/2 |c - c0|^2.
 // With LAMBDA, also lam = -dx dy [G^T (rho G c - rho v - mu) + alpha (c - c0)].
+// A hint to L2 for a line of global memory (no register is written, nothing waits on it).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// The TV kernels' threads walk kPPT pixels of a row one after another; asking L2 for the
+// later pixels' lines of the fields they read at the start lets those DRAM latencies
+// overlap the first pixel's work.  f[j] holds per[j] floats per pixel (NHWC).  Used by
+// the terminal adjoint and the multiplier update (measured faster); the trial objective
+// and the v-step measured slower or the same with it.
+template <int NF>
+__device__ __forceinline__ void prefetch_later_pixels(int bx, int r, const TvGeom& g,
+                                                      const float* const (&f)[NF],
+                                                      const int (&per)[NF]) {
+#pragma unroll
+  for (int i = 1; i < kPPT; ++i) {
+    const int q = bx * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
+    if (q < g.W) {
+      const size_t k = (size_t)r * g.W + q;
+#pragma unroll
+      for (int j = 0; j < NF; ++j)
+        if (f[j]) prefetch_l2(f[j] + k * per[j]);
+    }
+  }
+}
+
 // The per-thread part of one block (bx, by) of pixels; returns the thread's float32 sum.
 template <int CT, bool LAMBDA>
 __device__ __forceinline__ float objective_block(int bx, int by, const float* __restrict__ c,
@@ -146,6 +172,7 @@ __device__ __forceinline__ float terminal_block(int bx, int by, const float* __r
   float e_own[kPPT][CT];
   // Phase 1: the L~ terms of the thread's own pixels, and w at their cells.
   if (r < g.H) {
+    prefetch_later_pixels<4>(bx, r, g, {v, mu, c, c0}, {2 * CT, 2 * CT, CT, CT});
 #pragma unroll
     for (int i = 0; i < kPPT; ++i) {
       const int q = x0 + i * kTvBX + tx;
@@ -343,10 +370,6 @@ cudaError_t launch_pd_tv_step(const float* c, const float* mu, float* v, const T
 // a rounding boundary, and within one float32 ulp of the exact update.
 // Per-block partial sums: |v - Gc|^2, |G^T (v - v_prev)|^2, |c - c_prev|^2, |c|^2 and
 // K(c)/(dx dy) = sum |G c_i| + alpha/2 |c_i - c0_i|^2 (float32 terms, float64 blocks).
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 struct ResidualPair {
   float s, lo;  // v - k (a - b) = s + lo (to 2^-46 of the larger operand)
   float g;      // k (a - b) rounded: the gradient component for K(c)
@@ -431,21 +454,8 @@ __device__ __forceinline__ void alm_block(int bx, int by, const float* __restric
     const bool yin = r >= 1 && r <= g.H - 2;
     const float ky = yin ? g.inv2hy : 0.0f;
     const int up = yin ? g.W : 0;
-    // Ask L2 for the later pixels' lines now, so that their DRAM latency overlaps the
-    // first pixel's work (a hint: no register is written, nothing waits on it).
-#pragma unroll
-    for (int i = 1; i < kPPT; ++i) {
-      const int q = bx * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
-      if (q < g.W) {
-        const size_t k = (size_t)r * g.W + q;
-        prefetch_l2(v + k * 2 * C);
-        prefetch_l2(mu + k * 2 * C);
-        prefetch_l2(c + k * C);
-        prefetch_l2(c0 + k * C);
-        if (c_prev) prefetch_l2(c_prev + k * C);
-        if (v_prev) prefetch_l2(v_prev + k * 2 * C);
-      }
-    }
+    prefetch_later_pixels<6>(bx, r, g, {v, mu, c, c0, c_prev, v_prev},
+                             {2 * C, 2 * C, C, C, C, 2 * C});
 #pragma unroll
     for (int i = 0; i < kPPT; ++i) {
       const int q = bx * (kTvBX * kPPT) + i * kTvBX + threadIdx.x;
