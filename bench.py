@@ -625,8 +625,8 @@ def reduce_over_ranks(torch, dist, elapsed: float, pixel_steps: float, device):
 ORACLE_ROWS = 256           # one step of the reference arm: a 256 x 1024 band
 ORACLE_SAMPLE = (f"top {ORACLE_ROWS} rows of the 1024x1024x3 image (R=5): one Euler step, one "
                  "adjoint step, one v-step and one multiplier update, float64 NumPy, 1 thread")
-ORACLE_BASELINE_REPS = 2    # the GPU line's baseline: the whole image, twice (about 10 s)
-ORACLE_BASELINE_SAMPLE = (f"the whole 1024x1024x3 image (R=5), {ORACLE_BASELINE_REPS} times: one "
+ORACLE_WHOLE_REPS = 2    # the GPU line's baseline: the whole image, twice (about 10 s)
+ORACLE_WHOLE_SAMPLE = (f"the whole 1024x1024x3 image (R=5), {ORACLE_WHOLE_REPS} times: one "
                           "Euler step, one adjoint step, one v-step and one multiplier update "
                           "each, float64 NumPy, 1 thread")
 
@@ -967,11 +967,11 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         px = s = 0
-        for _ in range(ORACLE_BASELINE_REPS):
+        for _ in range(ORACLE_WHOLE_REPS):
             dpx, ds = oracle_sample(rows=H)
             px, s = px + dpx, s + ds
         cpu = {"value": px / s / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": ORACLE_BASELINE_SAMPLE,
+               "sample": ORACLE_WHOLE_SAMPLE,
                "host_cores": cpu_cores(), "seconds": s,
                "config1_solve": config1_solve(torch, lib, dev)}
 
