@@ -239,6 +239,13 @@ forward_tile_kernel(const float* __restrict__ c, float* __restrict__ out,
   float2* sm = smem2;
   float2* smask = smem2 + C * T::PLANE;
   const int x0 = blockIdx.x * T::TW, y0 = blockIdx.y * T::TH;
+  // Programmatic dependent launch: the next Euler step may be launched once every block
+  // of this one has started, and waits (in hardware) for this grid's completion before
+  // it reads c^{n+1}; launched without the attribute, both instructions do nothing.
+  // Every global read comes after the wait: the control of a trial sweep is written by the
+  // kernel just before its first step.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const float ex = (float)eps_n[0], ec = (float)eps_n[1];
   const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2;
   const float sk = colour_scale(0.5f * ec), mult = g.scale / sk;
@@ -370,6 +377,11 @@ adjoint_tile_kernel(const float* __restrict__ c, const float* __restrict__ lam,
   float2* sm = smem2;
   float2* smask = smem2 + 2 * C * T::PLANE;
   const int x0 = blockIdx.x * T::TW, y0 = blockIdx.y * T::TH;
+  // Programmatic dependent launch, as in forward_tile_kernel: the next adjoint step may
+  // be launched once every block of this one has started; all global reads follow the
+  // wait for the previous grid.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const float ex = (float)eps_n[0], ec = (float)eps_n[1];
   const float kx = 0.5f * ex * g.inv_w2, ky = 0.5f * ex * g.inv_h2, kc = 0.5f * ec;
   const bool border = load_tile<T, R, C, 2>(sm, smask, c, lam, g, x0, y0);

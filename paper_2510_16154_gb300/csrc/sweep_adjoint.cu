@@ -20,9 +20,17 @@ static cudaError_t adjoint_tiled(const float* c_n, const float* lam_next, float*
       attr_set = true;
     }
   }
-  dim3 grid(ceil_div(g.W, T::TW), ceil_div(g.H, T::TH));
-  kern<<<grid, dim3(kAdjBX, kAdjBY), smem, s>>>(c_n, lam_next, lam_out, eps_n, partial, g);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ceil_div(g.W, T::TW), ceil_div(g.H, T::TH));
+  cfg.blockDim = dim3(kAdjBX, kAdjBY);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, c_n, lam_next, lam_out, eps_n, partial, g);
 }
 
 static cudaError_t adjoint_generic(const float* c_n, const float* lam_next, float* lam_out,

@@ -19,9 +19,17 @@ static cudaError_t forward_tiled(const float* c_in, float* c_out, const double* 
       attr_set = true;
     }
   }
-  dim3 grid(ceil_div(g.W, T::TW), ceil_div(g.H, T::TH));
-  kern<<<grid, dim3(kFwdBX, kFwdBY), smem, s>>>(c_in, c_out, eps_n, g);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ceil_div(g.W, T::TW), ceil_div(g.H, T::TH));
+  cfg.blockDim = dim3(kFwdBX, kFwdBY);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, c_in, c_out, eps_n, g);
 }
 
 static cudaError_t forward_generic(const float* c_in, float* c_out, const double* eps_n,
