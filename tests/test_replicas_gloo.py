@@ -2,7 +2,8 @@
 its own image, the only collective is the whole-job timing).  The slowest rank's time
 and the sum of all ranks' pixel-steps give the aggregate; ranks get distinct images; the
 reference arm runs on rank 0 only.  Also the rule by which a timed region's clock record
-disqualifies it (measured once more)."""
+disqualifies it (measured once more), and the pair count behind the roofline's
+algorithmic flops against a brute-force enumeration."""
 import os
 import sys
 
@@ -69,3 +70,20 @@ def test_clock_record_rejection(clk, rejected):
     sys.path.insert(0, ROOT)
     import bench
     assert bench.clocks_rejected(clk) is rejected
+
+
+@pytest.mark.parametrize("h,w,r", [(1, 1, 1), (3, 5, 1), (7, 4, 2), (9, 9, 5), (6, 13, 3)])
+def test_roofline_pair_count_is_the_brute_force_count(h, w, r):
+    # The roofline numerator counts each unordered in-window pair of distinct in-image
+    # pixels once (window: |drow|, |dcol| <= r).  Enumerate the pairs directly.
+    sys.path.insert(0, ROOT)
+    import bench
+    pairs = 0
+    for i in range(h * w):
+        for j in range(i + 1, h * w):
+            (ri, ci), (rj, cj) = divmod(i, w), divmod(j, w)
+            if abs(ri - rj) <= r and abs(ci - cj) <= r:
+                pairs += 1
+    for c in (1, 3, 31):
+        assert bench.forward_flops_per_launch(h, w, c, r) == pairs * (7 * c + 9)
+        assert bench.adjoint_flops_per_launch(h, w, c, r) == pairs * (11 * c + 18)
